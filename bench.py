@@ -1,0 +1,402 @@
+"""Benchmark of the GB300 stable parallel merge.
+
+Workload (the large single stable merge): n = m = 2**28 int32 keys with
+int32 payloads in four seeded key distributions (uniform over the full int32
+range, uniform in [0, 1024), all keys equal, Zipf s = 1.2 over 2**20 values),
+plus the skewed lengths n = 2**28, m = 2**18 of the same four distributions:
+eight merges per step, both inputs pre-sorted.  Metric: merged key+value
+elements per second (n + m per merge), whole job.
+
+One step = for each of the eight inputs, Steps 1-2 (cross-rank search
+kernel) and Steps 3-4 (staged tile-merge kernel) through the C ABI
+(tm_cross_ranks + tm_merge_subproblems, the two kernels tm_merge launches).
+Inputs are resident in HBM; every merge reads 2-4 GB, far above the 129 MB
+L2, so no L2 flush is needed between iterations.
+
+Prints ONE JSON line on rank 0.  Under torchrun each rank runs an
+independent replica on its own GPU (the merge has no exchange step), and
+`value` counts the elements of all ranks over the slowest rank's time.
+
+--impl reference times the CPU oracle (the plain two-pointer stable merge
+of oracle/, single thread) on the same workload and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+import torch
+
+METRIC = "merged key+value elems/s and % of HBM peak, plain vs batched/learned, bit-exact"
+WORKLOAD = ("stable merge, int32 keys + int32 payloads: n=m=2^28 x {uniform_full, uniform_1024, "
+            "all_equal, zipf_1.2}, plus skewed n=2^28, m=2^18 x the same four; pre-sorted")
+UNIT = "elems/s"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1202_6575_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per output element of `kernel` from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    sha = kernel_source_sha()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        txt = open(path).read()
+        m_k = re.search(r"^kernel:\s*(\S+)", txt, re.M)
+        m_s = re.search(r"^source_sha:\s*(\S+)", txt, re.M)
+        m_b = re.search(r"^dram_bytes_per_output_element:\s*([0-9.]+)", txt, re.M)
+        if m_k and m_s and m_b and m_k.group(1) == kernel and m_s.group(1) == sha:
+            return float(m_b.group(1)), os.path.relpath(path, ROOT)
+    return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
+        self.gpu = gpu_index
+        self.proc = None
+        self.interval_ms = interval_ms
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms={self.interval_ms}"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self, power_floor_w: float = 0.0):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]),
+                             "power": float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             "hw": parts[5], "hw_thermal": parts[6], "sw_thermal": parts[7],
+                             "sw_power": parts[8]})
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = [r for r in rows if r["power"] >= power_floor_w] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hw_thermal", "hw_thermal_slowdown"),
+                              ("sw_thermal", "sw_thermal_slowdown"), ("sw_power", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in load])),
+                "sm_max_mhz": max(r["max"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(load)}
+
+
+def make_inputs(device, log2n=28, dists=None, skewed_too=True):
+    from paper_1202_6575_gb300 import workloads as W
+    items = []
+    for skewed in ((False, True) if skewed_too else (False,)):
+        for dist in (dists or W.DIST_NAMES):
+            A, Av, B, Bv = W.large_merge(dist, skewed, device, log2n=log2n, log2m_skewed=log2n - 10)
+            items.append({"name": f"{dist}{'_skewed' if skewed else ''}", "A": A, "Av": Av, "B": B, "Bv": Bv})
+    return items
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle on the host cores (rank 0 only; other ranks exit).
+
+    Each step merges a bounded sample of the workload: step k takes merge
+    k mod 8 of the workload restricted to the prefixes A[:a], B[:b] with
+    a : b = n : m, sized so that warmup + steps finish in about 90 s of CPU
+    time.  The two-pointer merge costs the same per element at any length,
+    so the rate carries over to the full workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    items = make_inputs(gen_dev, args.log2n, args.dists, not args.no_skewed)
+    hosts = [(it["A"].cpu().numpy(), it["Av"].cpu().numpy().view(np.uint32),
+              it["B"].cpu().numpy(), it["Bv"].cpu().numpy().view(np.uint32)) for it in items]
+    del items
+    # calibrate the single-thread rate on a 2**24-element prefix
+    A, Av, B, Bv = hosts[0]
+    t0 = time.perf_counter()
+    oracle.merge_two_pointer(A[:1 << 23], Av[:1 << 23], B[:1 << 23], Bv[:1 << 23])
+    rate = (1 << 24) / (time.perf_counter() - t0)
+    total_steps = args.steps + args.warmup
+    per_step = int(min(max(rate * 90.0 / total_steps, 1 << 20), len(A) + len(B)))
+
+    def step(k):
+        A, Av, B, Bv = hosts[k % len(hosts)]
+        n, m = len(A), len(B)
+        a = int(round(per_step * n / (n + m)))
+        b = min(m, per_step - a)
+        oracle.merge_two_pointer(A[:a], Av[:a], B[:b], Bv[:b])
+        return a + b
+
+    for k in range(args.warmup):
+        step(k)
+    elems = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        elems += step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = elems / dt
+    sample = (f"per step, prefixes of one of the eight merges (round robin) totalling {per_step} elements; "
+              f"single-thread two-pointer oracle (oracle/tm_oracle.c)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(items):
+    """Times the oracle, as it stands, on one merge of each input (host copies)."""
+    import oracle
+    oracle.build()
+    hosts = [(it["hA"], it["hAv"].view(np.uint32), it["hB"], it["hBv"].view(np.uint32)) for it in items]
+    elems = sum(len(h[0]) + len(h[2]) for h in hosts)
+    t0 = time.perf_counter()
+    for A, Av, B, Bv in hosts:
+        oracle.merge_two_pointer(A, Av, B, Bv)
+    dt = time.perf_counter() - t0
+    return {"value": elems / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "each of the eight merges once (the full workload, one pass), single-thread "
+                      "two-pointer merge of oracle/tm_oracle.c", "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--log2n", type=int, default=28, help="smaller cases for profiling only")
+    ap.add_argument("--dists", default="", help="comma list of distributions (default: all four)")
+    ap.add_argument("--no-skewed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.dists = [d for d in args.dists.split(",") if d] or None
+    rank, local_rank, world = env_rank()
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1202_6575_gb300 import tm
+
+    cfg = {}
+    if args.tile:
+        cfg["tile"] = args.tile
+    if args.threads:
+        cfg["threads"] = args.threads
+    cfg = cfg or None
+
+    items = make_inputs(dev, args.log2n, args.dists, not args.no_skewed)
+    for it in items:
+        n, m = it["A"].numel(), it["B"].numel()
+        it["n"], it["m"] = n, m
+        it["p"] = tm.tm_merge_blocks(n, m, cfg)
+        it["xbar"] = torch.empty(it["p"] + 1, dtype=torch.int64, device=dev)
+        it["ybar"] = torch.empty(it["p"] + 1, dtype=torch.int64, device=dev)
+    cmax = max(it["n"] + it["m"] for it in items)
+    C = torch.empty(cmax, dtype=torch.int32, device=dev)
+    Cv = torch.empty(cmax, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    elems_per_step = sum(it["n"] + it["m"] for it in items)
+    bytes_merge_per_step = sum(2 * (it["n"] + it["m"]) * 8 for it in items)
+
+    # per-merge events: search start, merge start, merge end
+    def step(evs=None):
+        for k, it in enumerate(items):
+            n, m = it["n"], it["m"]
+            if evs is not None:
+                evs[k][0].record(stream)
+            tm.tm_cross_ranks("i32", it["A"], it["B"], it["p"], it["xbar"], it["ybar"], stream=stream)
+            if evs is not None:
+                evs[k][1].record(stream)
+            tm.tm_merge_subproblems("i32", it["A"], it["Av"], it["B"], it["Bv"], it["p"], it["xbar"], it["ybar"],
+                                    C[:n + m], Cv[:n + m], status, cfg=cfg, stream=stream)
+            if evs is not None:
+                evs[k][2].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    assert tm.tm_read_status(status) == 0
+
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in items] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with sampler:
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    assert tm.tm_read_status(status) == 0
+    search_ms = sum(e[0].elapsed_time(e[1]) for st in evs for e in st)
+    merge_ms = sum(e[1].elapsed_time(e[2]) for st in evs for e in st)
+    per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][1].elapsed_time(evs[s][k][2]) for s in range(args.steps)]))
+                         for k, it in enumerate(items)}
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    value = elems_per_step * args.steps * world / (elapsed_max / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    launches = len(items) * args.steps
+    achieved = (bytes_merge_per_step * args.steps / launches) / ((merge_ms / launches) / 1e3) / 1e9
+    traffic_per_elem, traffic_src = profile_traffic("tile_merge_kernel")
+    traffic = None if traffic_per_elem is None else traffic_per_elem * elems_per_step / len(items)
+    roofline = {"bound": "hbm", "kernel": "tile_merge_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "traffic": traffic, "traffic_source": traffic_src,
+                "algorithmic_bytes_per_launch": bytes_merge_per_step / len(items),
+                "search_share": search_ms / (search_ms + merge_ms)}
+
+    # End to end: pinned host inputs -> device, merge through tm_merge, result -> host.
+    e2e = None
+    cpu = None
+    if not args.no_e2e:
+        pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t)
+        for it in items:
+            it["hA"], it["hAv"], it["hB"], it["hBv"] = (pin(it["A"]).numpy(), pin(it["Av"]).numpy(),
+                                                        pin(it["B"]).numpy(), pin(it["Bv"]).numpy())
+        hC = torch.empty(cmax, dtype=torch.int32, pin_memory=True)
+        hCv = torch.empty(cmax, dtype=torch.int32, pin_memory=True)
+        ws = tm.new_workspace(max(tm.tm_merge_workspace_size(it["n"], it["m"], cfg) for it in items), dev)
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            h2d = d2h = 0
+            for it in items:
+                n, m = it["n"], it["m"]
+                A = it["A"]; Av = it["Av"]; B = it["B"]; Bv = it["Bv"]
+                A.copy_(torch.from_numpy(it["hA"]), non_blocking=True)
+                Av.copy_(torch.from_numpy(it["hAv"]), non_blocking=True)
+                B.copy_(torch.from_numpy(it["hB"]), non_blocking=True)
+                Bv.copy_(torch.from_numpy(it["hBv"]), non_blocking=True)
+                tm.tm_merge("i32", A, Av, B, Bv, C[:n + m], Cv[:n + m], ws, cfg=cfg, stream=stream)
+                hC[:n + m].copy_(C[:n + m], non_blocking=True)
+                hCv[:n + m].copy_(Cv[:n + m], non_blocking=True)
+                h2d += 2 * (n + m) * 4
+                d2h += 2 * (n + m) * 4
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": elems_per_step * args.e2e_steps * world / (float(te.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "pinned host -> tm_merge (C ABI) -> pinned host, one stream"}
+        assert tm.tm_read_status(ws) == 0
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(items)
+
+    clocks = sampler.summary(power_floor_w=200.0)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "elements_per_step": elems_per_step,
+                           "merges_per_step": len(items), "tile": args.tile or 4096,
+                           "threads": args.threads or 256, "l2": "inputs larger than L2 (2-4 GB per merge)",
+                           "parallelism": f"replicas x{world}"},
+                "per_merge_ms": per_item_merge_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 2 * len(items) * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

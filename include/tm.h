@@ -1,0 +1,172 @@
+/*
+ * tm.h -- C ABI of the GB300 (sm_103a) stable parallel merge library.
+ *
+ * The library implements the merge of Traeff, "Simplified, stable parallel
+ * merging" (arXiv:1202.6575):
+ *   Steps 1-2  (Section 2): cross ranks of the p block starts of A in B
+ *              (rank_low) and of B in A (rank_high), by binary search;
+ *   Steps 3-4  (Section 2): the 2p disjoint subproblems those ranks define
+ *              (cases (a)-(e) and their B-side mirror), each merged stably;
+ *   Section 3: the same merge applied to many pairs at once, and the stable
+ *              merge sort built from it.
+ * A learned cross-rank proposal (not in the paper) narrows the rank_high
+ * searches of a large, repeatedly merged base array to a short window that
+ * is verified against the definition of rank_high and replaced by the full
+ * search when the check fails.
+ *
+ * Conventions for every entry point:
+ *  - Key arrays are non-decreasing under the key type's order: TM_KEY_U32 and
+ *    TM_KEY_U64 unsigned, TM_KEY_I32 signed, TM_KEY_F32 IEEE '<' (no NaN;
+ *    -0.0 and +0.0 are equal keys).  Payloads are opaque 32-bit words that
+ *    travel with their keys.  Arrays are structure-of-arrays.
+ *  - Stability (Section 2): on equal keys every element of A precedes every
+ *    element of B, and each side keeps its input order.  A and B are never
+ *    exchanged.  The output is therefore unique.
+ *  - All pointers named *_keys, *_vals, workspace, offsets, xbar, ybar,
+ *    status and model are DEVICE pointers owned by the caller, except where
+ *    a comment says "host".  Key pointers must be aligned to the key size,
+ *    payload pointers to 4 bytes, workspace and model to 256 bytes.  Outputs
+ *    must not overlap inputs.  The library allocates no device memory.
+ *  - Every call is asynchronous on `stream` (NULL = the legacy default
+ *    stream) and returns after enqueueing work.  Argument errors return
+ *    TM_ERR_INVALID / TM_ERR_WORKSPACE / TM_ERR_UNSUPPORTED synchronously and
+ *    launch nothing; a failed launch returns TM_ERR_CUDA.  Conditions that
+ *    only the device can see (a subproblem larger than its staging buffer, a
+ *    bounded wait that gave up) are written to a device status word that
+ *    tm_read_status() returns; kernels never trap.
+ *  - Lengths are element counts (int64_t, >= 0).  Empty inputs are valid.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TM_API __attribute__((visibility("default")))
+#else
+#define TM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* tm_stream_t;
+
+typedef enum {
+    TM_OK = 0,
+    TM_ERR_INVALID = 1,      /* bad argument (NULL, negative length, misaligned pointer, ...) */
+    TM_ERR_UNSUPPORTED = 2,  /* unknown key type or configuration outside the kernel's limits */
+    TM_ERR_WORKSPACE = 3,    /* workspace NULL or smaller than the matching *_workspace_size() */
+    TM_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    TM_ERR_TIMEOUT = 5,      /* device: a bounded wait gave up (set in the status word) */
+    TM_ERR_BOUNDS = 6        /* device: a subproblem exceeded its staging capacity */
+} tm_status;
+
+typedef enum {
+    TM_KEY_U32 = 0,
+    TM_KEY_I32 = 1,
+    TM_KEY_U64 = 2,
+    TM_KEY_F32 = 3
+} tm_key_type;
+
+/* Tuning knobs.  A NULL tm_config*, or 0 in a field, selects the default. */
+typedef struct tm_config {
+    int64_t p;          /* blocks per input array (Section 2).  0: derived so that one
+                           subproblem fits `tile` elements: p = ceil((n + m) / tile). */
+    int32_t tile;       /* max elements (A piece + B piece) a CTA stages in shared memory;
+                           default 4096 */
+    int32_t threads;    /* threads per CTA (multiple of 32, 64..512); default 256.  The
+                           CTA re-splits its subproblem into `threads` blocks per side by
+                           the same rank_low / rank_high rule. */
+    int32_t grid;       /* CTAs of the persistent kernels; default: resident CTAs per SM
+                           x SM count */
+    int32_t reserved;
+} tm_config;
+
+/* Human-readable name of a status code (static storage). */
+TM_API const char* tm_status_str(tm_status s);
+
+/* Library version, for the binding's load check. */
+TM_API int tm_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Device status word                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Copies the 32-bit device status word at `status` (device) to the host after
+ * synchronising `stream`.  Returns TM_OK when no kernel reported a problem,
+ * otherwise the first device-side code (TM_ERR_BOUNDS, TM_ERR_TIMEOUT).
+ * For tm_merge the status word is the first 4 bytes of its workspace; for the
+ * batched and sort calls likewise. */
+TM_API tm_status tm_read_status(const void* status, tm_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Single merge (Section 2, Steps 1-4)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* The number of blocks p that tm_merge uses for (n, m, cfg). */
+TM_API int64_t tm_merge_blocks(int64_t n, int64_t m, const tm_config* cfg);
+
+/* Workspace bytes tm_merge needs: a 256-byte status header and the two
+ * cross-rank arrays xbar[0..p], ybar[0..p] (int64). */
+TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg);
+
+/* Stable merge of A (n keys + payloads) and B (m) into C (n + m).
+ * Steps 1-2 run as one search kernel (2p binary searches), the stream order
+ * is the single synchronisation of Section 2, and Steps 3-4 run as one
+ * staged tile-merge kernel with one CTA per subproblem.  The workspace holds
+ * the status word (cleared by this call) and the cross ranks. */
+TM_API tm_status tm_merge(tm_key_type kt,
+                   const void* a_keys, const uint32_t* a_vals, int64_t n,
+                   const void* b_keys, const uint32_t* b_vals, int64_t m,
+                   void* c_keys, uint32_t* c_vals,
+                   void* workspace, size_t workspace_bytes,
+                   const tm_config* cfg, tm_stream_t stream);
+
+/* Steps 1 and 2 alone (Section 2): xbar[i] = rank_low(A[x_i], B) for i < p,
+ * xbar[p] = m; ybar[j] = rank_high(B[y_j], A) for j < p, ybar[p] = n, with
+ * the block starts x_i, y_j of Section 2 (the first n mod p blocks one
+ * longer).  The start of an empty block is the +inf sentinel, so its cross
+ * rank is the other array's length.  xbar and ybar hold p + 1 int64 each. */
+TM_API tm_status tm_cross_ranks(tm_key_type kt,
+                         const void* a_keys, int64_t n,
+                         const void* b_keys, int64_t m, int64_t p,
+                         int64_t* xbar, int64_t* ybar, tm_stream_t stream);
+
+/* Steps 3 and 4 alone: given the cross ranks of tm_cross_ranks for the same
+ * (A, B, p), merges the 2p subproblems into C.  `status` is a device int32
+ * the kernel sets on a device-side error (not cleared here).  cfg->p is
+ * ignored (p is the argument). */
+TM_API tm_status tm_merge_subproblems(tm_key_type kt,
+                               const void* a_keys, const uint32_t* a_vals, int64_t n,
+                               const void* b_keys, const uint32_t* b_vals, int64_t m,
+                               int64_t p, const int64_t* xbar, const int64_t* ybar,
+                               void* c_keys, uint32_t* c_vals, int32_t* status,
+                               const tm_config* cfg, tm_stream_t stream);
+
+/* The subproblems of Steps 3-4 as the device computes them: for k < p the
+ * A-side processing element k, for k >= p the B-side one (k - p).  Row k of
+ * `table` (device, 2p x 4 int64) receives a0, a1, b0, b1: the half-open A and
+ * B ranges of the subproblem; its output starts at C[a0 + b0].  Used to check
+ * the device's reading of the five cases against the paper's worked example
+ * and the host oracle. */
+TM_API tm_status tm_subproblems(int64_t n, int64_t m, int64_t p,
+                                const int64_t* xbar, const int64_t* ybar,
+                                int64_t* table, tm_stream_t stream);
+
+/* Batched rank search: out[k] = rank_low(q[k], X) (kind 0) or
+ * rank_high(q[k], X) (kind 1) for k < count, by binary search (Section 2's
+ * definitions).  q need not be sorted. */
+TM_API tm_status tm_rank_search(tm_key_type kt, int kind,
+                         const void* q, int64_t count,
+                         const void* x_keys, int64_t len,
+                         int64_t* out, tm_stream_t stream);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif /* TM_H */

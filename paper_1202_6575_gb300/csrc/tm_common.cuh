@@ -1,0 +1,239 @@
+// Shared device helpers of the stable parallel merge (sm_103a).
+//
+// Notation follows Traeff, "Simplified, stable parallel merging", Section 2:
+// A[0..n), B[0..m) non-decreasing, p blocks per array, block starts x_i / y_j
+// (the first len mod p blocks one element longer), cross ranks
+// xbar_i = rank_low(A[x_i], B) and ybar_j = rank_high(B[y_j], A).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tm.h"
+
+namespace pmerge {
+
+// ---------------------------------------------------------------------------
+// Key types
+// ---------------------------------------------------------------------------
+// Native C++ '<' gives exactly the orders of the ABI: unsigned for uint32_t
+// and uint64_t, signed for int32_t, IEEE for float (-0.0 == +0.0).
+
+template <typename K> struct KeyOf;
+template <> struct KeyOf<uint32_t> { static constexpr tm_key_type id = TM_KEY_U32; };
+template <> struct KeyOf<int32_t>  { static constexpr tm_key_type id = TM_KEY_I32; };
+template <> struct KeyOf<uint64_t> { static constexpr tm_key_type id = TM_KEY_U64; };
+template <> struct KeyOf<float>    { static constexpr tm_key_type id = TM_KEY_F32; };
+
+inline size_t key_size(tm_key_type kt) { return (kt == TM_KEY_U64) ? 8 : 4; }
+
+// ---------------------------------------------------------------------------
+// Block decomposition (Section 2)
+// ---------------------------------------------------------------------------
+
+// x_i for 0 <= i <= p: i*ceil(len/p) for i < r = len mod p, else
+// i*floor(len/p) + r (so x_p = len).
+template <typename I>
+__host__ __device__ __forceinline__ I block_start(I len, I p, I i) {
+    I q = len / p, r = len - q * p;
+    return (i < r) ? i * (q + 1) : i * q + r;
+}
+
+// Block holding index k (0 <= k <= len); k = len is "block p".  The O(1)
+// rule of Section 2, with the empty-block case (floor(len/p) = 0) covered by
+// k >= r*ceil(len/p) = len.
+template <typename I>
+__host__ __device__ __forceinline__ I block_of(I len, I p, I k) {
+    if (k >= len) return p;
+    I q = len / p, r = len - q * p;
+    I head = r * (q + 1);
+    return (k < head) ? k / (q + 1) : (k - head) / q + r;
+}
+
+// Smallest block index j whose start y_j is >= k (0 <= k <= len): the block
+// of k, or the next one when k lies strictly inside its block.
+template <typename I>
+__host__ __device__ __forceinline__ I first_block_at_or_after(I len, I p, I k) {
+    I j = block_of(len, p, k);
+    return (block_start(len, p, j) == k) ? j : j + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Rank primitives (Section 2)
+// ---------------------------------------------------------------------------
+// rank_low(x, X)  = #{k : X[k] <  x}  (the i with X[i-1] <  x <= X[i])
+// rank_high(x, X) = #{k : X[k] <= x}  (the j with X[j-1] <= x <  X[j])
+
+template <typename K, typename I>
+__device__ __forceinline__ I rank_low_global(const K* __restrict__ X, I len, K x) {
+    I lo = 0;
+    while (len > 0) {
+        I half = len >> 1;
+        if (__ldg(X + lo + half) < x) { lo += half + 1; len -= half + 1; }
+        else                           { len = half; }
+    }
+    return lo;
+}
+
+template <typename K, typename I>
+__device__ __forceinline__ I rank_high_global(const K* __restrict__ X, I len, K x) {
+    I lo = 0;
+    while (len > 0) {
+        I half = len >> 1;
+        if (!(x < __ldg(X + lo + half))) { lo += half + 1; len -= half + 1; }
+        else                             { len = half; }
+    }
+    return lo;
+}
+
+template <typename K>
+__device__ __forceinline__ int rank_low_smem(const K* X, int len, K x) {
+    int lo = 0;
+    while (len > 0) {
+        int half = len >> 1;
+        if (X[lo + half] < x) { lo += half + 1; len -= half + 1; }
+        else                  { len = half; }
+    }
+    return lo;
+}
+
+template <typename K>
+__device__ __forceinline__ int rank_high_smem(const K* X, int len, K x) {
+    int lo = 0;
+    while (len > 0) {
+        int half = len >> 1;
+        if (!(x < X[lo + half])) { lo += half + 1; len -= half + 1; }
+        else                     { len = half; }
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Subproblem of one processing element, by the split-point form of Steps 3-4
+// ---------------------------------------------------------------------------
+// The points P_A(i) = (x_i, xbar_i), P_B(j) = (ybar_j, y_j) and (n, m) lie on
+// the merge path and, by Observation 1, form one chain ordered by a + b (the
+// output offset).  The subproblem of A-PE i runs from P_A(i) to the next
+// point of the chain: P_B(j') with j' the first B block starting at or after
+// xbar_i, if y_j' < xbar_{i+1}, else P_A(i+1).  This is exactly cases (a)-(e)
+// of Step 3:  (a) xbar_i = xbar_{i+1} -> no B point between;  (e) xbar_i = y_j
+// -> next is P_B(j);  (b)/(d) -> P_A(i+1);  (c) -> P_B(j+1).  Step 4 is the
+// mirror.  Returns the A range [a0, a1), B range [b0, b1); the output starts
+// at a0 + b0.
+
+template <typename I, typename LoadXbar, typename LoadYbar>
+__device__ __forceinline__ void subproblem_of(bool a_side, I pe, I n, I m, I p,
+                                              LoadXbar xbar, LoadYbar ybar,
+                                              I& a0, I& a1, I& b0, I& b1) {
+    if (a_side) {
+        I xi = block_start(n, p, pe), xi1 = block_start(n, p, pe + 1);
+        I xb = xbar(pe), xb1 = xbar(pe + 1);
+        a0 = xi; b0 = xb;
+        I jn = first_block_at_or_after(m, p, xb);
+        I yjn = block_start(m, p, jn);
+        if (jn < p && yjn < xb1) { a1 = ybar(jn); b1 = yjn; }
+        else                     { a1 = xi1;      b1 = xb1; }
+    } else {
+        I yj = block_start(m, p, pe), yj1 = block_start(m, p, pe + 1);
+        I yb = ybar(pe), yb1 = ybar(pe + 1);
+        b0 = yj; a0 = yb;
+        I in = first_block_at_or_after(n, p, yb);
+        I xin = block_start(n, p, in);
+        if (in < p && xin < yb1) { b1 = xbar(in); a1 = xin; }
+        else                     { b1 = yj1;      a1 = yb1; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device status word
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy (TMA engine) wrappers, inline PTX for sm_90+.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier; gives up after `limit_ns`
+// nanoseconds of global time and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// Bulk global -> shared copy; completion is counted on `bar` in bytes.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Bulk shared -> global copy in the current bulk group.
+__device__ __forceinline__ void bulk_s2g(void* gmem_dst, const void* smem_src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 :: "l"(gmem_dst), "r"(smem_u32(smem_src)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until at most N committed bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" :: "n"(N) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group %0;" :: "n"(N) : "memory");
+}
+
+// Wait time for one tile's bulk loads before a kernel reports TM_ERR_TIMEOUT
+// (a tile normally lands in microseconds).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+}  // namespace pmerge

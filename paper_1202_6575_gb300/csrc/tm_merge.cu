@@ -1,0 +1,365 @@
+// Single stable merge (Section 2): the cross-rank search kernel (Steps 1-2)
+// and the staged tile-merge kernel (Steps 3-4), plus their C-ABI entry
+// points.
+#include <algorithm>
+
+#include "tm_host.h"
+#include "tm_tile.cuh"
+
+namespace pmerge {
+
+// ---------------------------------------------------------------------------
+// Steps 1-2: cross-rank search kernel
+// ---------------------------------------------------------------------------
+// Thread t < p:      xbar[t] = rank_low(A[x_t], B)      (x_t = n -> m)
+// Thread p + t:      ybar[t] = rank_high(B[y_t], A)     (y_t = m -> n)
+// Thread 2p:         xbar[p] = m, ybar[p] = n.
+// Each search is ceil(log2(len + 1)) dependent probes; the probes of
+// neighbouring threads share the upper levels of the search tree in L2.
+template <typename K>
+__global__ void __launch_bounds__(256)
+cross_rank_kernel(const K* __restrict__ A, int64_t n, const K* __restrict__ B, int64_t m,
+                  int64_t p, int64_t* __restrict__ xbar, int64_t* __restrict__ ybar) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < p) {
+        int64_t xi = block_start<int64_t>(n, p, t);
+        xbar[t] = (xi < n) ? rank_low_global<K, int64_t>(B, m, __ldg(A + xi)) : m;
+    } else if (t < 2 * p) {
+        int64_t j = t - p;
+        int64_t yj = block_start<int64_t>(m, p, j);
+        ybar[j] = (yj < m) ? rank_high_global<K, int64_t>(A, n, __ldg(B + yj)) : n;
+    } else if (t == 2 * p) {
+        xbar[p] = m;
+        ybar[p] = n;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256)
+rank_search_kernel(const K* __restrict__ q, int64_t count, const K* __restrict__ X, int64_t len,
+                   int kind, int64_t* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    K x = __ldg(q + t);
+    out[t] = kind ? rank_high_global<K, int64_t>(X, len, x) : rank_low_global<K, int64_t>(X, len, x);
+}
+
+__global__ void __launch_bounds__(256)
+subproblem_table_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restrict__ xbar,
+                        const int64_t* __restrict__ ybar, int64_t* __restrict__ table) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * p) return;
+    auto xb = [&](int64_t i) { return xbar[i]; };
+    auto yb = [&](int64_t j) { return ybar[j]; };
+    int64_t a0, a1, b0, b1;
+    subproblem_of<int64_t>(k < p, k < p ? k : k - p, n, m, p, xb, yb, a0, a1, b0, b1);
+    table[4 * k + 0] = a0; table[4 * k + 1] = a1;
+    table[4 * k + 2] = b0; table[4 * k + 3] = b1;
+}
+
+// ---------------------------------------------------------------------------
+// Steps 3-4: one CTA per subproblem
+// ---------------------------------------------------------------------------
+
+template <typename K>
+struct MergeArgs {
+    const K* A; const uint32_t* Av; int64_t n;
+    const K* B; const uint32_t* Bv; int64_t m;
+    K* C; uint32_t* Cv;
+    int64_t p;
+    const int64_t* xbar; const int64_t* ybar;
+    int32_t* status;
+    int capA, capB;
+    TileLayout lay;
+};
+
+template <typename K>
+__global__ void __launch_bounds__(kMaxThreads)
+tile_merge_kernel(const MergeArgs<K> g) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int64_t item = blockIdx.x;
+    const bool a_side = item < g.p;
+    const int64_t pe = a_side ? item : item - g.p;
+
+    int64_t a0, a1, b0, b1;
+    auto xbar = [&](int64_t i) { return __ldg(g.xbar + i); };
+    auto ybar = [&](int64_t j) { return __ldg(g.ybar + j); };
+    subproblem_of<int64_t>(a_side, pe, g.n, g.m, g.p, xbar, ybar, a0, a1, b0, b1);
+    const int64_t nA64 = a1 - a0, nB64 = b1 - b0;
+    if (nA64 < 0 || nB64 < 0 || nA64 > g.capA || nB64 > g.capB) {
+        if (tid == 0) set_status(g.status, TM_ERR_BOUNDS);
+        return;
+    }
+    const int nA = (int)nA64, nB = (int)nB64;
+    if (nA + nB == 0) return;
+
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    uint8_t* rkA = smem + g.lay.off_kA; uint8_t* rvA = smem + g.lay.off_vA;
+    uint8_t* rkB = smem + g.lay.off_kB; uint8_t* rvB = smem + g.lay.off_vB;
+    uint8_t* rkC = smem + g.lay.off_kC; uint8_t* rvC = smem + g.lay.off_vC;
+
+    const StageWin wkA = stage_window(g.A, g.n, a0, a1, sizeof(K));
+    const StageWin wvA = stage_window(g.Av, g.n, a0, a1, 4);
+    const StageWin wkB = stage_window(g.B, g.m, b0, b1, sizeof(K));
+    const StageWin wvB = stage_window(g.Bv, g.m, b0, b1, 4);
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+        uint32_t tx = wkA.bulk_bytes() + wvA.bulk_bytes() + wkB.bulk_bytes() + wvB.bulk_bytes();
+        mbar_arrive_expect_tx(bar, tx);
+        stage_issue(rkA, wkA, bar);
+        stage_issue(rvA, wvA, bar);
+        stage_issue(rkB, wkB, bar);
+        stage_issue(rvB, wvB, bar);
+    }
+    stage_edges<K>(rkA, wkA, tid, T);
+    stage_edges<uint32_t>(rvA, wvA, tid, T);
+    stage_edges<K>(rkB, wkB, tid, T);
+    stage_edges<uint32_t>(rvB, wvB, tid, T);
+    __syncthreads();                                   // barrier initialised before anyone waits
+    bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) set_status(g.status, TM_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, kWaitLimitNs);       // let copies in flight land before exit
+        return;
+    }
+
+    TileView<K> v;
+    v.kA = reinterpret_cast<K*>(rkA) + wkA.head;
+    v.vA = reinterpret_cast<uint32_t*>(rvA) + wvA.head;
+    v.kB = reinterpret_cast<K*>(rkB) + wkB.head;
+    v.vB = reinterpret_cast<uint32_t*>(rvB) + wvB.head;
+    const OutWin ok_ = out_window(g.C, a0 + b0, nA + nB, sizeof(K));
+    const OutWin ov_ = out_window(g.Cv, a0 + b0, nA + nB, 4);
+    v.kC = reinterpret_cast<K*>(rkC + ok_.mis);
+    v.vC = reinterpret_cast<uint32_t*>(rvC + ov_.mis);
+    v.xs = reinterpret_cast<int*>(smem + g.lay.off_split);
+    v.ys = v.xs + (T + 1);
+
+    tile_resplit_and_merge<K>(v, nA, nB);
+
+    if (tid == 0) {
+        out_issue(ok_, rkC);
+        out_issue(ov_, rvC);
+        bulk_commit();
+    }
+    out_edges<K>(ok_, rkC, tid, T);
+    out_edges<uint32_t>(ov_, rvC, tid, T);
+    if (tid == 0) bulk_wait_read<0>();                 // smem must outlive the bulk store's reads
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+static int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int64_t choose_blocks(int64_t n, int64_t m, const tm_config* cfg) {
+    if (cfg && cfg->p > 0) return cfg->p;
+    int64_t tile = (cfg && cfg->tile > 0) ? cfg->tile : kDefaultTile;
+    int64_t p = ceil_div64(n + m, tile);
+    return p < 1 ? 1 : p;
+}
+
+int choose_threads(const tm_config* cfg) {
+    return (cfg && cfg->threads > 0) ? cfg->threads : kDefaultThreads;
+}
+
+template <typename K>
+static tm_status launch_tile_merge(const K* A, const uint32_t* Av, int64_t n,
+                                   const K* B, const uint32_t* Bv, int64_t m,
+                                   int64_t p, const int64_t* xbar, const int64_t* ybar,
+                                   K* C, uint32_t* Cv, int32_t* status,
+                                   const tm_config* cfg, cudaStream_t s) {
+    MergeArgs<K> g;
+    g.A = A; g.Av = Av; g.n = n; g.B = B; g.Bv = Bv; g.m = m; g.C = C; g.Cv = Cv;
+    g.p = p; g.xbar = xbar; g.ybar = ybar; g.status = status;
+    g.capA = (int)ceil_div64(n, p);
+    g.capB = (int)ceil_div64(m, p);
+    const int T = choose_threads(cfg);
+    if (T < 64 || T > kMaxThreads || (T % 32) != 0) return TM_ERR_UNSUPPORTED;
+    if (ceil_div64(n, p) + ceil_div64(m, p) > (int64_t)kMaxTileElems) return TM_ERR_UNSUPPORTED;
+    g.lay = make_tile_layout(g.capA, g.capB, sizeof(K), T);
+    if (g.lay.bytes > kMaxSmemBytes) return TM_ERR_UNSUPPORTED;
+    if (!ensure_smem_limit(tile_merge_kernel<K>, g.lay.bytes)) return TM_ERR_UNSUPPORTED;
+    if (2 * p > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    tile_merge_kernel<K><<<(unsigned)(2 * p), T, g.lay.bytes, s>>>(g);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+template <typename K>
+static tm_status launch_cross_ranks(const K* A, int64_t n, const K* B, int64_t m, int64_t p,
+                                    int64_t* xbar, int64_t* ybar, cudaStream_t s) {
+    int64_t threads = 2 * p + 1;
+    int64_t blocks = ceil_div64(threads, 256);
+    if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    cross_rank_kernel<K><<<(unsigned)blocks, 256, 0, s>>>(A, n, B, m, p, xbar, ybar);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+size_t merge_workspace_bytes(int64_t p) {
+    return kStatusBytes + 2 * align_up((size_t)(p + 1) * sizeof(int64_t), 256);
+}
+
+template <typename K>
+static tm_status merge_typed(const void* a_keys, const uint32_t* a_vals, int64_t n,
+                             const void* b_keys, const uint32_t* b_vals, int64_t m,
+                             void* c_keys, uint32_t* c_vals, void* ws, int64_t p,
+                             const tm_config* cfg, cudaStream_t s) {
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    int32_t* status = reinterpret_cast<int32_t*>(w);
+    int64_t* xbar = reinterpret_cast<int64_t*>(w + kStatusBytes);
+    int64_t* ybar = reinterpret_cast<int64_t*>(w + kStatusBytes + align_up((size_t)(p + 1) * 8, 256));
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (n + m == 0) return TM_OK;
+    const K* A = static_cast<const K*>(a_keys);
+    const K* B = static_cast<const K*>(b_keys);
+    tm_status st = launch_cross_ranks<K>(A, n, B, m, p, xbar, ybar, s);
+    if (st != TM_OK) return st;
+    return launch_tile_merge<K>(A, a_vals, n, B, b_vals, m, p, xbar, ybar,
+                                static_cast<K*>(c_keys), c_vals, status, cfg, s);
+}
+
+}  // namespace pmerge
+
+using namespace pmerge;
+
+extern "C" {
+
+const char* tm_status_str(tm_status s) {
+    switch (s) {
+        case TM_OK: return "ok";
+        case TM_ERR_INVALID: return "invalid argument";
+        case TM_ERR_UNSUPPORTED: return "unsupported key type or configuration";
+        case TM_ERR_WORKSPACE: return "workspace missing or too small";
+        case TM_ERR_CUDA: return "CUDA error";
+        case TM_ERR_TIMEOUT: return "device wait timed out";
+        case TM_ERR_BOUNDS: return "subproblem exceeded its staging capacity";
+    }
+    return "unknown status";
+}
+
+int tm_version(void) { return kVersion; }
+
+tm_status tm_read_status(const void* status, tm_stream_t stream) {
+    if (!status) return TM_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TM_ERR_CUDA;
+    int32_t h = 0;
+    if (cudaMemcpy(&h, status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return TM_ERR_CUDA;
+    return static_cast<tm_status>(h);
+}
+
+int64_t tm_merge_blocks(int64_t n, int64_t m, const tm_config* cfg) {
+    if (n < 0 || m < 0) return -1;
+    return choose_blocks(n, m, cfg);
+}
+
+size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg) {
+    if (n < 0 || m < 0) return 0;
+    return merge_workspace_bytes(choose_blocks(n, m, cfg));
+}
+
+tm_status tm_merge(tm_key_type kt,
+                   const void* a_keys, const uint32_t* a_vals, int64_t n,
+                   const void* b_keys, const uint32_t* b_vals, int64_t m,
+                   void* c_keys, uint32_t* c_vals,
+                   void* workspace, size_t workspace_bytes,
+                   const tm_config* cfg, tm_stream_t stream) {
+    if (n < 0 || m < 0) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
+        (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
+        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+        return TM_ERR_INVALID;
+    const int64_t p = choose_blocks(n, m, cfg);
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p))
+        return TM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return merge_typed<uint32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_I32: return merge_typed<int32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_U64: return merge_typed<uint64_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_F32: return merge_typed<float>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+tm_status tm_cross_ranks(tm_key_type kt, const void* a_keys, int64_t n,
+                         const void* b_keys, int64_t m, int64_t p,
+                         int64_t* xbar, int64_t* ybar, tm_stream_t stream) {
+    if (n < 0 || m < 0 || p < 1 || !xbar || !ybar) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) ||
+        !aligned(xbar, 8) || !aligned(ybar, 8))
+        return TM_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return launch_cross_ranks<uint32_t>((const uint32_t*)a_keys, n, (const uint32_t*)b_keys, m, p, xbar, ybar, s);
+        case TM_KEY_I32: return launch_cross_ranks<int32_t>((const int32_t*)a_keys, n, (const int32_t*)b_keys, m, p, xbar, ybar, s);
+        case TM_KEY_U64: return launch_cross_ranks<uint64_t>((const uint64_t*)a_keys, n, (const uint64_t*)b_keys, m, p, xbar, ybar, s);
+        case TM_KEY_F32: return launch_cross_ranks<float>((const float*)a_keys, n, (const float*)b_keys, m, p, xbar, ybar, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+tm_status tm_merge_subproblems(tm_key_type kt,
+                               const void* a_keys, const uint32_t* a_vals, int64_t n,
+                               const void* b_keys, const uint32_t* b_vals, int64_t m,
+                               int64_t p, const int64_t* xbar, const int64_t* ybar,
+                               void* c_keys, uint32_t* c_vals, int32_t* status,
+                               const tm_config* cfg, tm_stream_t stream) {
+    if (n < 0 || m < 0 || p < 1 || !xbar || !ybar) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
+        (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
+        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+        return TM_ERR_INVALID;
+    if (n + m == 0) return TM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return launch_tile_merge<uint32_t>((const uint32_t*)a_keys, a_vals, n, (const uint32_t*)b_keys, b_vals, m, p, xbar, ybar, (uint32_t*)c_keys, c_vals, status, cfg, s);
+        case TM_KEY_I32: return launch_tile_merge<int32_t>((const int32_t*)a_keys, a_vals, n, (const int32_t*)b_keys, b_vals, m, p, xbar, ybar, (int32_t*)c_keys, c_vals, status, cfg, s);
+        case TM_KEY_U64: return launch_tile_merge<uint64_t>((const uint64_t*)a_keys, a_vals, n, (const uint64_t*)b_keys, b_vals, m, p, xbar, ybar, (uint64_t*)c_keys, c_vals, status, cfg, s);
+        case TM_KEY_F32: return launch_tile_merge<float>((const float*)a_keys, a_vals, n, (const float*)b_keys, b_vals, m, p, xbar, ybar, (float*)c_keys, c_vals, status, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+tm_status tm_subproblems(int64_t n, int64_t m, int64_t p, const int64_t* xbar,
+                         const int64_t* ybar, int64_t* table, tm_stream_t stream) {
+    if (n < 0 || m < 0 || p < 1 || !aligned(xbar, 8) || !aligned(ybar, 8) || !aligned(table, 8))
+        return TM_ERR_INVALID;
+    int64_t blocks = (2 * p + 255) / 256;
+    if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    subproblem_table_kernel<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        n, m, p, xbar, ybar, table);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+tm_status tm_rank_search(tm_key_type kt, int kind, const void* q, int64_t count,
+                         const void* x_keys, int64_t len, int64_t* out, tm_stream_t stream) {
+    if (count < 0 || len < 0 || (kind != 0 && kind != 1)) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    if (count == 0) return TM_OK;
+    const size_t E = key_size(kt);
+    if (!aligned(q, E) || (len > 0 && !aligned(x_keys, E)) || !aligned(out, 8)) return TM_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    switch (kt) {
+        case TM_KEY_U32: rank_search_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>((const uint32_t*)q, count, (const uint32_t*)x_keys, len, kind, out); break;
+        case TM_KEY_I32: rank_search_kernel<int32_t><<<(unsigned)blocks, 256, 0, s>>>((const int32_t*)q, count, (const int32_t*)x_keys, len, kind, out); break;
+        case TM_KEY_U64: rank_search_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>((const uint64_t*)q, count, (const uint64_t*)x_keys, len, kind, out); break;
+        case TM_KEY_F32: rank_search_kernel<float><<<(unsigned)blocks, 256, 0, s>>>((const float*)q, count, (const float*)x_keys, len, kind, out); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+"""Python binding of libtm.so, the C ABI declared in include/tm.h.
+
+Argument marshalling only: every function here checks tensor devices, dtypes
+and contiguity, turns tensors into device pointers and the current torch
+stream into a cudaStream_t, and calls the C entry point of the same name.
+All computation runs in the library's CUDA kernels.  There is no CPU path:
+if libtm.so is missing or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtm.so")
+
+KEY_TYPES = {"u32": 0, "i32": 1, "u64": 2, "f32": 3}
+KEY_BYTES = {"u32": 4, "i32": 4, "u64": 8, "f32": 4}
+TORCH_KEY_DTYPES = {"u32": (torch.int32,), "i32": (torch.int32,), "u64": (torch.int64,),
+                    "f32": (torch.float32,)}
+
+TM_OK = 0
+TM_ERR_INVALID = 1
+TM_ERR_UNSUPPORTED = 2
+TM_ERR_WORKSPACE = 3
+TM_ERR_CUDA = 4
+TM_ERR_TIMEOUT = 5
+TM_ERR_BOUNDS = 6
+
+
+class TmConfig(ctypes.Structure):
+    """struct tm_config of include/tm.h (0 = default in every field)."""
+    _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class TmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {tm_status_str(code)} (status {code})")
+
+
+_lib = None
+_I64, _I32, _SZ, _P = ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_void_p
+
+# name -> (restype, argtypes); the ABI of include/tm.h.
+_SIGNATURES = {
+    "tm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "tm_version": (ctypes.c_int, []),
+    "tm_read_status": (ctypes.c_int, [_P, _P]),
+    "tm_merge_blocks": (_I64, [_I64, _I64, _P]),
+    "tm_merge_workspace_size": (_SZ, [_I64, _I64, _P]),
+    "tm_merge": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _SZ, _P, _P]),
+    "tm_cross_ranks": (ctypes.c_int, [ctypes.c_int, _P, _I64, _P, _I64, _I64, _P, _P, _P]),
+    "tm_merge_subproblems": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _I64, _P, _P,
+                                            _P, _P, _P, _P, _P]),
+    "tm_rank_search": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _P, _P]),
+    "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
+}
+
+
+def load():
+    """Loads libtm.so (built by paper_1202_6575_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_1202_6575_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def tm_status_str(code: int) -> str:
+    return load().tm_status_str(int(code)).decode()
+
+
+def tm_version() -> int:
+    return int(load().tm_version())
+
+
+def _check(code: int, where: str):
+    if code != TM_OK:
+        raise TmError(code, where)
+
+
+def _cfg(cfg):
+    if cfg is None:
+        return None
+    if isinstance(cfg, TmConfig):
+        return ctypes.byref(cfg)
+    c = TmConfig()
+    for k, v in dict(cfg).items():
+        setattr(c, k, int(v))
+    return ctypes.byref(c)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtypes=None) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    return t.data_ptr() if t.numel() else 0
+
+
+def _kt(kt: str) -> int:
+    try:
+        return KEY_TYPES[kt]
+    except KeyError:
+        raise ValueError(f"unknown key type {kt!r}") from None
+
+
+# ---------------------------------------------------------------------------
+# Single merge
+# ---------------------------------------------------------------------------
+
+def tm_merge_blocks(n: int, m: int, cfg=None) -> int:
+    return int(load().tm_merge_blocks(n, m, _cfg(cfg)))
+
+
+def tm_merge_workspace_size(n: int, m: int, cfg=None) -> int:
+    return int(load().tm_merge_workspace_size(n, m, _cfg(cfg)))
+
+
+def new_workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, stream=None):
+    """Stable merge of (A, Av) and (B, Bv); returns (C, Cv, workspace).
+    The status word is the first 4 bytes of the workspace (tm_read_status)."""
+    kd = TORCH_KEY_DTYPES[kt]
+    n, m = A.numel(), B.numel()
+    if C is None:
+        C = torch.empty(n + m, dtype=A.dtype, device=A.device)
+    if Cv is None:
+        Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
+    if C.numel() != n + m or Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m:
+        raise ValueError("length mismatch")
+    cfgp = _cfg(cfg)
+    if workspace is None:
+        workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)
+    code = load().tm_merge(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd), _dev(Bv, "Bv"), m,
+                           _dev(C, "C", kd), _dev(Cv, "Cv"), _dev(workspace, "workspace"),
+                           workspace.numel(), cfgp, _stream(stream))
+    _check(code, "tm_merge")
+    return C, Cv, workspace
+
+
+def tm_cross_ranks(kt: str, A, B, p: int, xbar=None, ybar=None, stream=None):
+    """Steps 1-2: returns (xbar, ybar), int64 tensors of p + 1 entries."""
+    kd = TORCH_KEY_DTYPES[kt]
+    if xbar is None:
+        xbar = torch.empty(p + 1, dtype=torch.int64, device=A.device)
+    if ybar is None:
+        ybar = torch.empty(p + 1, dtype=torch.int64, device=A.device)
+    code = load().tm_cross_ranks(_kt(kt), _dev(A, "A", kd), A.numel(), _dev(B, "B", kd), B.numel(), p,
+                                 _dev(xbar, "xbar", (torch.int64,)), _dev(ybar, "ybar", (torch.int64,)),
+                                 _stream(stream))
+    _check(code, "tm_cross_ranks")
+    return xbar, ybar
+
+
+def tm_merge_subproblems(kt: str, A, Av, B, Bv, p: int, xbar, ybar, C=None, Cv=None, status=None,
+                         cfg=None, stream=None):
+    """Steps 3-4 given the cross ranks; returns (C, Cv, status)."""
+    kd = TORCH_KEY_DTYPES[kt]
+    n, m = A.numel(), B.numel()
+    if C is None:
+        C = torch.empty(n + m, dtype=A.dtype, device=A.device)
+    if Cv is None:
+        Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    code = load().tm_merge_subproblems(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd),
+                                       _dev(Bv, "Bv"), m, p, _dev(xbar, "xbar", (torch.int64,)),
+                                       _dev(ybar, "ybar", (torch.int64,)), _dev(C, "C", kd), _dev(Cv, "Cv"),
+                                       _dev(status, "status", (torch.int32,)), _cfg(cfg), _stream(stream))
+    _check(code, "tm_merge_subproblems")
+    return C, Cv, status
+
+
+def tm_rank_search(kt: str, kind: str, q, X, out=None, stream=None):
+    """out[k] = rank_low(q[k], X) (kind 'low') or rank_high(q[k], X) ('high')."""
+    kd = TORCH_KEY_DTYPES[kt]
+    if out is None:
+        out = torch.empty(q.numel(), dtype=torch.int64, device=q.device)
+    code = load().tm_rank_search(_kt(kt), {"low": 0, "high": 1}[kind], _dev(q, "q", kd), q.numel(),
+                                 _dev(X, "X", kd), X.numel(), _dev(out, "out", (torch.int64,)),
+                                 _stream(stream))
+    _check(code, "tm_rank_search")
+    return out
+
+
+def tm_subproblems(n: int, m: int, p: int, xbar, ybar, table=None, stream=None):
+    """Device-computed subproblem table, int64 (2p, 4): a0, a1, b0, b1."""
+    if table is None:
+        table = torch.empty((2 * p, 4), dtype=torch.int64, device=xbar.device)
+    code = load().tm_subproblems(n, m, p, _dev(xbar, "xbar", (torch.int64,)), _dev(ybar, "ybar", (torch.int64,)),
+                                 _dev(table, "table", (torch.int64,)), _stream(stream))
+    _check(code, "tm_subproblems")
+    return table
+
+
+def tm_read_status(status, stream=None) -> int:
+    """Synchronises the stream and returns the device status word (0 = ok)."""
+    return int(load().tm_read_status(_dev(status, "status"), _stream(stream)))

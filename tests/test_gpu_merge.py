@@ -1,0 +1,166 @@
+"""GPU parity of the single stable merge (Steps 1-4) against the CPU oracle.
+
+Every comparison is bit-exact: keys and payloads (payload = source tag |
+index, so equal keys must come out A first and in input order)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1202_6575_gb300 import tm, workloads as W
+from tests.helpers import to_np, vals_np, first_mismatch
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "figure1.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_merge_check(kt, A, Av, B, Bv, cfg=None, offset_a=0, offset_b=0, offset_c=0):
+    """Runs tm_merge on the GPU (optionally on sub-views shifted by a few
+    elements, to exercise unaligned starts) and compares with the oracle."""
+    def shifted(t, off):
+        if off == 0:
+            return t.to(DEV)
+        big = torch.empty(t.numel() + off, dtype=t.dtype, device=DEV)
+        big[off:] = t.to(DEV)
+        return big[off:]
+    dA, dAv, dB, dBv = shifted(A, offset_a), shifted(Av, offset_a), shifted(B, offset_b), shifted(Bv, offset_b)
+    n, m = A.numel(), B.numel()
+    Cb = torch.empty(n + m + offset_c, dtype=A.dtype, device=DEV)
+    Cvb = torch.empty(n + m + offset_c, dtype=torch.int32, device=DEV)
+    C, Cv, ws = tm.tm_merge(kt, dA, dAv, dB, dBv, Cb[offset_c:], Cvb[offset_c:], cfg=cfg)
+    assert tm.tm_read_status(ws) == 0
+    K, V = oracle.merge_two_pointer(to_np(A, kt), vals_np(Av), to_np(B, kt), vals_np(Bv))
+    ck, cv = to_np(C, kt), vals_np(Cv)
+    assert first_mismatch(ck, K) is None, f"key mismatch at {first_mismatch(ck, K)}"
+    assert first_mismatch(cv, V) is None, f"payload mismatch at {first_mismatch(cv, V)}"
+
+
+def test_figure1_cross_ranks_and_subproblems():
+    g = json.load(open(GOLDEN))
+    A = torch.tensor(g["A"], dtype=torch.int32, device=DEV)
+    B = torch.tensor(g["B"], dtype=torch.int32, device=DEV)
+    p = g["p"]
+    xbar, ybar = tm.tm_cross_ranks("u32", A, B, p)
+    assert xbar.tolist() == g["xbar"] and ybar.tolist() == g["ybar"]
+    table = tm.tm_subproblems(len(g["A"]), len(g["B"]), p, xbar, ybar).cpu().numpy()
+    otable = oracle.subproblems(len(g["A"]), len(g["B"]), p, np.array(g["xbar"]), np.array(g["ybar"]))
+    for k in range(2 * p):
+        lo, hi, olo, ohi, c0, case = otable[k]
+        a0, a1, b0, b1 = table[k]
+        if k < p:
+            assert (a0, a1, b0, b1) == (lo, hi, olo, ohi)
+        else:
+            assert (b0, b1, a0, a1) == (lo, hi, olo, ohi)
+        assert a0 + b0 == c0
+    Av = W.payload(0, len(g["A"]), "cpu")
+    Bv = W.payload(1, len(g["B"]), "cpu")
+    gpu_merge_check("u32", A.cpu(), Av, B.cpu(), Bv, cfg={"p": p, "threads": 64})
+
+
+def test_subproblem_table_matches_five_cases_exhaustively():
+    rng = np.random.default_rng(0)
+    for trial in range(300):
+        n, m = int(rng.integers(0, 40)), int(rng.integers(0, 40))
+        p = int(rng.integers(1, 14))
+        alpha = int(rng.choice([1, 3, 30]))
+        A = np.sort(rng.integers(0, alpha, n)).astype(np.uint32)
+        B = np.sort(rng.integers(0, alpha, m)).astype(np.uint32)
+        xb_o, yb_o = oracle.cross_ranks(A, B, p)
+        dA = torch.from_numpy(A.view(np.int32)).to(DEV)
+        dB = torch.from_numpy(B.view(np.int32)).to(DEV)
+        xbar, ybar = tm.tm_cross_ranks("u32", dA, dB, p)
+        assert xbar.cpu().numpy().tolist() == xb_o.tolist()
+        assert ybar.cpu().numpy().tolist() == yb_o.tolist()
+        table = tm.tm_subproblems(n, m, p, xbar, ybar).cpu().numpy()
+        otable = oracle.subproblems(n, m, p, xb_o, yb_o)
+        for k in range(2 * p):
+            lo, hi, olo, ohi, c0, case = otable[k]
+            a0, a1, b0, b1 = table[k]
+            got = (a0, a1, b0, b1) if k < p else (b0, b1, a0, a1)
+            assert got == (lo, hi, olo, ohi), (n, m, p, k, got, otable[k])
+
+
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+@pytest.mark.parametrize("n,m", [(0, 0), (0, 7), (9, 0), (1, 1), (5, 3), (1000, 1), (4097, 4095),
+                                 (30001, 20011), (100000, 3)])
+def test_small_merges_all_key_types(kt, n, m):
+    for alphabet in (None, 7):
+        A, Av, B, Bv = W.small_merge(n, m, kt, seed=n * 31 + m, alphabet=alphabet)
+        gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 1024})
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+@pytest.mark.parametrize("tile", [256, 1000, 4096, 8192])
+def test_tile_and_thread_shapes(threads, tile):
+    A, Av, B, Bv = W.small_merge(70001, 50003, "u32", seed=tile + threads, alphabet=500)
+    gpu_merge_check("u32", A, Av, B, Bv, cfg={"tile": tile, "threads": threads})
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("offs", [(1, 0, 0), (0, 3, 1), (2, 1, 3), (3, 3, 2)])
+def test_unaligned_starts(kt, offs):
+    A, Av, B, Bv = W.small_merge(12345, 6789, kt, seed=sum(offs), alphabet=100)
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 512}, offset_a=offs[0], offset_b=offs[1], offset_c=offs[2])
+
+
+def test_explicit_p_larger_than_n():
+    A, Av, B, Bv = W.small_merge(10, 300, "u32", seed=5, alphabet=20)
+    gpu_merge_check("u32", A, Av, B, Bv, cfg={"p": 64})
+    gpu_merge_check("u32", B, Bv, A, Av, cfg={"p": 64})
+
+
+@pytest.mark.parametrize("dist", W.DIST_NAMES)
+def test_distributions_small(dist):
+    for skewed in (False, True):
+        A, Av, B, Bv = W.large_merge(dist, skewed, "cpu", log2n=17, log2m_skewed=9)
+        gpu_merge_check("i32", A, Av, B, Bv)
+
+
+def test_single_merge_1m_p1024():
+    """n = 2**20, m = 2**19 u32 keys in [0, 2**16), p = 1024."""
+    A, Av, B, Bv = W.single_merge_1m(DEV)
+    p = 1024
+    xbar, ybar = tm.tm_cross_ranks("u32", A, B, p)
+    xo, yo = oracle.cross_ranks(to_np(A, "u32"), to_np(B, "u32"), p)
+    assert np.array_equal(xbar.cpu().numpy(), xo) and np.array_equal(ybar.cpu().numpy(), yo)
+    gpu_merge_check("u32", A.cpu(), Av.cpu(), B.cpu(), Bv.cpu(), cfg={"p": p})
+
+
+def test_rank_search_against_oracle():
+    rng = np.random.default_rng(7)
+    X = np.sort(rng.integers(0, 1000, 50000)).astype(np.uint32)
+    q = rng.integers(0, 1100, 3000).astype(np.uint32)
+    dX = torch.from_numpy(X.view(np.int32)).to(DEV)
+    dq = torch.from_numpy(q.view(np.int32)).to(DEV)
+    lo = tm.tm_rank_search("u32", "low", dq, dX).cpu().numpy()
+    hi = tm.tm_rank_search("u32", "high", dq, dX).cpu().numpy()
+    assert lo.tolist() == [oracle.rank_low(v, X) for v in q]
+    assert hi.tolist() == [oracle.rank_high(v, X) for v in q]
+
+
+@pytest.mark.parametrize("dist", W.DIST_NAMES)
+@pytest.mark.parametrize("skewed", [False, True])
+def test_large_merge_full_size(dist, skewed):
+    """n = m = 2**28 (or n = 2**28, m = 2**18) int32 keys, the default launch
+    configuration the benchmark times; every output element compared."""
+    A, Av, B, Bv = W.large_merge(dist, skewed, DEV)
+    C, Cv, ws = tm.tm_merge("i32", A, Av, B, Bv)
+    assert tm.tm_read_status(ws) == 0
+    hA, hAv, hB, hBv = to_np(A, "i32"), vals_np(Av), to_np(B, "i32"), vals_np(Bv)
+    del A, Av, B, Bv
+    ck, cv = to_np(C, "i32"), vals_np(Cv)
+    del C, Cv
+    torch.cuda.empty_cache()
+    K, V = oracle.merge_two_pointer(hA, hAv, hB, hBv)
+    assert first_mismatch(ck, K) is None, f"key mismatch at {first_mismatch(ck, K)}"
+    assert first_mismatch(cv, V) is None, f"payload mismatch at {first_mismatch(cv, V)}"
