@@ -157,6 +157,32 @@ TM_API tm_status tm_subproblems(int64_t n, int64_t m, int64_t p,
                                 const int64_t* xbar, const int64_t* ybar,
                                 int64_t* table, tm_stream_t stream);
 
+/* Stable merge that allocates nothing and needs no workspace.  The paper has
+ * no counterpart; this is a convenience of the library.  It exists for
+ * callers that cannot call cudaMalloc or hand the library a workspace: code
+ * hosted by a framework that passes it only its input and output buffers,
+ * loops that must never hit the allocator (an allocation can block or
+ * synchronise the device), or processes whose device memory is fully
+ * reserved.  The computation and the result are those of tm_merge.
+ *
+ * The cross ranks live in one file-scope device array inside the library,
+ * 4 MiB, which every GPU that loads the library keeps until the process
+ * exits.  It holds p + 1 <= 262144 entries per side, so (n, m, cfg) must give
+ * tm_merge_blocks() <= 262143 (about 2^30 elements at the default tile);
+ * larger requests return TM_ERR_WORKSPACE and launch nothing.
+ * The first call on each device looks the array's device address up once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: two
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other's result, so keep calls ordered on one stream.
+ * `status` (device int32, may be NULL) is an output: the call clears it and
+ * a kernel sets it on a device-side error, as the status word of tm_merge. */
+TM_API tm_status tm_merge_noalloc(tm_key_type kt,
+                                  const void* a_keys, const uint32_t* a_vals, int64_t n,
+                                  const void* b_keys, const uint32_t* b_vals, int64_t m,
+                                  void* c_keys, uint32_t* c_vals, int32_t* status,
+                                  const tm_config* cfg, tm_stream_t stream);
+
 /* Batched rank search: out[k] = rank_low(q[k], X) (kind 0) or
  * rank_high(q[k], X) (kind 1) for k < count, by binary search (Section 2's
  * definitions).  q need not be sorted. */

@@ -2,6 +2,7 @@
 // and the staged tile-merge kernel (Steps 3-4), plus their C-ABI entry
 // points.
 #include <algorithm>
+#include <mutex>
 
 #include "tm_host.h"
 #include "tm_tile.cuh"
@@ -363,3 +364,79 @@ tm_status tm_rank_search(tm_key_type kt, int kind, const void* q, int64_t count,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Merge without allocation: the cross ranks live in a file-scope device array
+// ---------------------------------------------------------------------------
+// For callers that can neither allocate device memory nor supply a workspace.
+// The array is part of this module, so every GPU that loads the library
+// holds it (4 MiB) until the process exits.
+
+namespace pmerge {
+
+constexpr int64_t kNoAllocMaxBlocks = 262143;            // p + 1 <= 262144 per side
+
+static __device__ __align__(256) int64_t g_noalloc_ranks[2 * (kNoAllocMaxBlocks + 1)];
+
+// Device address of g_noalloc_ranks on the current device, looked up once per
+// device (the host-side name of a __device__ array is not a device address).
+static int64_t* noalloc_ranks_ptr() {
+    static std::mutex mu;
+    static int64_t* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_ranks) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<int64_t*>(p);
+    }
+    return addr[dev];
+}
+
+template <typename K>
+static tm_status merge_noalloc_typed(const void* a_keys, const uint32_t* a_vals, int64_t n,
+                                     const void* b_keys, const uint32_t* b_vals, int64_t m,
+                                     void* c_keys, uint32_t* c_vals, int32_t* status,
+                                     int64_t p, const tm_config* cfg, cudaStream_t s) {
+    int64_t* ranks = noalloc_ranks_ptr();
+    if (!ranks) return TM_ERR_CUDA;
+    int64_t* xbar = ranks;
+    int64_t* ybar = ranks + (kNoAllocMaxBlocks + 1);
+    if (status && cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (n + m == 0) return TM_OK;
+    const K* A = static_cast<const K*>(a_keys);
+    const K* B = static_cast<const K*>(b_keys);
+    tm_status st = launch_cross_ranks<K>(A, n, B, m, p, xbar, ybar, s);
+    if (st != TM_OK) return st;
+    return launch_tile_merge<K>(A, a_vals, n, B, b_vals, m, p, xbar, ybar,
+                                static_cast<K*>(c_keys), c_vals, status, cfg, s);
+}
+
+}  // namespace pmerge
+
+extern "C" tm_status tm_merge_noalloc(tm_key_type kt,
+                                      const void* a_keys, const uint32_t* a_vals, int64_t n,
+                                      const void* b_keys, const uint32_t* b_vals, int64_t m,
+                                      void* c_keys, uint32_t* c_vals, int32_t* status,
+                                      const tm_config* cfg, tm_stream_t stream) {
+    using namespace pmerge;
+    if (n < 0 || m < 0) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
+        (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
+        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))) ||
+        (status && !aligned(status, 4)))
+        return TM_ERR_INVALID;
+    const int64_t p = choose_blocks(n, m, cfg);
+    if (p > kNoAllocMaxBlocks) return TM_ERR_WORKSPACE;   // beyond the built-in array
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return merge_noalloc_typed<uint32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, status, p, cfg, s);
+        case TM_KEY_I32: return merge_noalloc_typed<int32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, status, p, cfg, s);
+        case TM_KEY_U64: return merge_noalloc_typed<uint64_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, status, p, cfg, s);
+        case TM_KEY_F32: return merge_noalloc_typed<float>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, status, p, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}

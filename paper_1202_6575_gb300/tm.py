@@ -58,6 +58,7 @@ _SIGNATURES = {
                                             _P, _P, _P, _P, _P]),
     "tm_rank_search": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _P, _P]),
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
+    "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
 }
 
 
@@ -225,3 +226,20 @@ def tm_subproblems(n: int, m: int, p: int, xbar, ybar, table=None, stream=None):
 def tm_read_status(status, stream=None) -> int:
     """Synchronises the stream and returns the device status word (0 = ok)."""
     return int(load().tm_read_status(_dev(status, "status"), _stream(stream)))
+
+
+def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream=None):
+    """tm_merge without a workspace: the library keeps the cross ranks in its
+    own built-in device array, so the call itself allocates nothing.  C, Cv
+    (and the optional int32 `status`) are outputs the caller provides.
+    Calls share that array: keep them ordered on one stream."""
+    kd = TORCH_KEY_DTYPES[kt]
+    n, m = A.numel(), B.numel()
+    if C.numel() != n + m or Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m:
+        raise ValueError("length mismatch")
+    code = load().tm_merge_noalloc(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd),
+                                   _dev(Bv, "Bv"), m, _dev(C, "C", kd), _dev(Cv, "Cv"),
+                                   None if status is None else _dev(status, "status", (torch.int32,)),
+                                   _cfg(cfg), _stream(stream))
+    _check(code, "tm_merge_noalloc")
+    return C, Cv
