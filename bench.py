@@ -8,8 +8,11 @@ eight merges per step, both inputs pre-sorted.  Metric: merged key+value
 elements per second (n + m per merge), whole job.
 
 One step = for each of the eight inputs, Steps 1-2 (cross-rank search
-kernel) and Steps 3-4 (staged tile-merge kernel) through the C ABI
-(tm_cross_ranks + tm_merge_subproblems, the two kernels tm_merge launches).
+kernel), Steps 3-4 selection (planning kernel: one tile record per
+subproblem) and Steps 3-4 merges (persistent staged tile-merge kernel),
+through the C ABI phase calls tm_cross_ranks, tm_plan_subproblems and
+tm_merge_tiles: the kernels tm_merge launches, with CUDA events between
+them.
 Inputs are resident in HBM; every merge reads 2-4 GB, far above the 129 MB
 L2, so no L2 flush is needed between iterations.
 
@@ -227,6 +230,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--split", type=int, default=0, help="in-CTA split: 1 blocks (paper's rule), 2 diagonal")
     ap.add_argument("--log2n", type=int, default=28, help="smaller cases for profiling only")
     ap.add_argument("--dists", default="", help="comma list of distributions (default: all four)")
     ap.add_argument("--no-skewed", action="store_true")
@@ -255,6 +260,10 @@ def main():
         cfg["tile"] = args.tile
     if args.threads:
         cfg["threads"] = args.threads
+    if args.stages:
+        cfg["stages"] = args.stages
+    if args.split:
+        cfg["split"] = args.split
     cfg = cfg or None
 
     items = make_inputs(dev, args.log2n, args.dists, not args.no_skewed)
@@ -264,34 +273,40 @@ def main():
         it["p"] = tm.tm_merge_blocks(n, m, cfg)
         it["xbar"] = torch.empty(it["p"] + 1, dtype=torch.int64, device=dev)
         it["ybar"] = torch.empty(it["p"] + 1, dtype=torch.int64, device=dev)
+        it["tiles"] = torch.empty(2 * it["p"] * tm.tm_tile_record_bytes(), dtype=torch.uint8, device=dev)
+        it["cap"] = tm.tm_merge_tile_cap(n, m, it["p"])
+        it["count"] = tm.tm_plan_tile_count(n, m, it["p"])
+    control = torch.zeros(256, dtype=torch.uint8, device=dev)
     cmax = max(it["n"] + it["m"] for it in items)
     C = torch.empty(cmax, dtype=torch.int32, device=dev)
     Cv = torch.empty(cmax, dtype=torch.int32, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     elems_per_step = sum(it["n"] + it["m"] for it in items)
     bytes_merge_per_step = sum(2 * (it["n"] + it["m"]) * 8 for it in items)
 
-    # per-merge events: search start, merge start, merge end
+    # per-merge events: search start, plan start, merge start, merge end
     def step(evs=None):
         for k, it in enumerate(items):
-            n, m = it["n"], it["m"]
+            n, m, p = it["n"], it["m"], it["p"]
             if evs is not None:
                 evs[k][0].record(stream)
-            tm.tm_cross_ranks("i32", it["A"], it["B"], it["p"], it["xbar"], it["ybar"], stream=stream)
+            tm.tm_cross_ranks("i32", it["A"], it["B"], p, it["xbar"], it["ybar"], stream=stream)
             if evs is not None:
                 evs[k][1].record(stream)
-            tm.tm_merge_subproblems("i32", it["A"], it["Av"], it["B"], it["Bv"], it["p"], it["xbar"], it["ybar"],
-                                    C[:n + m], Cv[:n + m], status, cfg=cfg, stream=stream)
+            tm.tm_plan_subproblems(n, m, p, it["xbar"], it["ybar"], it["tiles"], cfg=cfg, stream=stream)
             if evs is not None:
                 evs[k][2].record(stream)
+            tm.tm_merge_tiles("i32", it["A"], it["Av"], it["B"], it["Bv"], it["tiles"], it["count"], it["cap"],
+                              C[:n + m], Cv[:n + m], control, cfg=cfg, stream=stream)
+            if evs is not None:
+                evs[k][3].record(stream)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
-    assert tm.tm_read_status(status) == 0
+    assert tm.tm_read_status(control) == 0
 
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in items] for _ in range(args.steps)]
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in items] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
@@ -307,10 +322,11 @@ def main():
     if world > 1:
         dist.barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
-    assert tm.tm_read_status(status) == 0
+    assert tm.tm_read_status(control) == 0
     search_ms = sum(e[0].elapsed_time(e[1]) for st in evs for e in st)
-    merge_ms = sum(e[1].elapsed_time(e[2]) for st in evs for e in st)
-    per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][1].elapsed_time(evs[s][k][2]) for s in range(args.steps)]))
+    plan_ms = sum(e[1].elapsed_time(e[2]) for st in evs for e in st)
+    merge_ms = sum(e[2].elapsed_time(e[3]) for st in evs for e in st)
+    per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][2].elapsed_time(evs[s][k][3]) for s in range(args.steps)]))
                          for k, it in enumerate(items)}
 
     t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
@@ -322,13 +338,14 @@ def main():
     peak, peak_kind = measured_peaks()
     launches = len(items) * args.steps
     achieved = (bytes_merge_per_step * args.steps / launches) / ((merge_ms / launches) / 1e3) / 1e9
-    traffic_per_elem, traffic_src = profile_traffic("tile_merge_kernel")
+    traffic_per_elem, traffic_src = profile_traffic("merge_engine_kernel")
     traffic = None if traffic_per_elem is None else traffic_per_elem * elems_per_step / len(items)
-    roofline = {"bound": "hbm", "kernel": "tile_merge_kernel", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "merge_engine_kernel", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "traffic": traffic, "traffic_source": traffic_src,
                 "algorithmic_bytes_per_launch": bytes_merge_per_step / len(items),
-                "search_share": search_ms / (search_ms + merge_ms)}
+                "search_share": search_ms / (search_ms + plan_ms + merge_ms),
+                "plan_share": plan_ms / (search_ms + plan_ms + merge_ms)}
 
     # End to end: pinned host inputs -> device, merge through tm_merge, result -> host.
     e2e = None
@@ -387,12 +404,14 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "elements_per_step": elems_per_step,
-                           "merges_per_step": len(items), "tile": args.tile or 4096,
-                           "threads": args.threads or 256, "l2": "inputs larger than L2 (2-4 GB per merge)",
+                           "merges_per_step": len(items), "tile": args.tile or 2048,
+                           "blocks_p": items[0]["p"],
+                           "threads": args.threads or 128, "stages": args.stages or "auto",
+                           "split": {0: "diagonal (default)", 1: "blocks", 2: "diagonal"}[args.split], "l2": "inputs larger than L2 (2-4 GB per merge)",
                            "parallelism": f"replicas x{world}"},
                 "per_merge_ms": per_item_merge_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 2 * len(items) * args.steps}
+                "gpu_launches": 3 * len(items) * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

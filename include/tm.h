@@ -77,14 +77,28 @@ typedef struct tm_config {
     int64_t p;          /* blocks per input array (Section 2).  0: derived so that one
                            subproblem fits `tile` elements: p = ceil((n + m) / tile). */
     int32_t tile;       /* max elements (A piece + B piece) a CTA stages in shared memory;
-                           default 4096 */
-    int32_t threads;    /* threads per CTA (multiple of 32, 64..512); default 256.  The
-                           CTA re-splits its subproblem into `threads` blocks per side by
-                           the same rank_low / rank_high rule. */
+                           default 2048 */
+    int32_t threads;    /* consumer threads per CTA: 128 or 256 (512 with TM_SPLIT_BLOCKS);
+                           default 128 */
     int32_t grid;       /* CTAs of the persistent kernels; default: resident CTAs per SM
                            x SM count */
+    int32_t stages;     /* input stages of the persistent tile kernel (1, 2 or 4); default 2
+                           (1 when two do not fit in shared memory) */
+    int32_t split;      /* how a CTA divides its staged tile among its threads:
+                           TM_SPLIT_DIAGONAL (2; also 0 = default) or TM_SPLIT_BLOCKS (1) */
     int32_t reserved;
 } tm_config;
+
+/* In-CTA split modes.  TM_SPLIT_BLOCKS applies the paper's rule again inside
+ * the CTA: `threads` blocks per piece, rank_low of every A-block start in the
+ * B piece, rank_high of every B-block start in the A piece, and the 2*threads
+ * sub-subproblems of Steps 3-4, two per thread.  TM_SPLIT_DIAGONAL gives every
+ * thread the same number of outputs: thread t starts at output t*ceil(L/threads)
+ * of the tile, at the split the position formulas of Section 2 fix there
+ * (i A elements before it: B[d-i-1] < A[i] and A[i-1] <= B[d-i]).  Both give
+ * the identical (unique) stable merge.  A tile longer than 33 runs per thread
+ * (tile > 33 * threads) uses TM_SPLIT_BLOCKS. */
+enum { TM_SPLIT_BLOCKS = 1, TM_SPLIT_DIAGONAL = 2, TM_SPLIT_DEFAULT = TM_SPLIT_DIAGONAL };
 
 /* Human-readable name of a status code (static storage). */
 TM_API const char* tm_status_str(tm_status s);
@@ -110,15 +124,18 @@ TM_API tm_status tm_read_status(const void* status, tm_stream_t stream);
 /* The number of blocks p that tm_merge uses for (n, m, cfg). */
 TM_API int64_t tm_merge_blocks(int64_t n, int64_t m, const tm_config* cfg);
 
-/* Workspace bytes tm_merge needs: a 256-byte status header and the two
- * cross-rank arrays xbar[0..p], ybar[0..p] (int64). */
+/* Workspace bytes tm_merge needs: a 256-byte control block (status word,
+ * work-queue counter), the two cross-rank arrays xbar[0..p], ybar[0..p]
+ * (int64) and the 2p tile records. */
 TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg);
 
 /* Stable merge of A (n keys + payloads) and B (m) into C (n + m).
  * Steps 1-2 run as one search kernel (2p binary searches), the stream order
- * is the single synchronisation of Section 2, and Steps 3-4 run as one
- * staged tile-merge kernel with one CTA per subproblem.  The workspace holds
- * the status word (cleared by this call) and the cross ranks. */
+ * is the single synchronisation of Section 2, and Steps 3-4 run as a
+ * planning kernel (one tile record per subproblem) and the persistent
+ * staged tile-merge kernel.  Equivalent to tm_cross_ranks,
+ * tm_plan_subproblems and tm_merge_tiles on the workspace's arrays.  The
+ * status word (first 4 bytes of the workspace) is cleared by this call. */
 TM_API tm_status tm_merge(tm_key_type kt,
                    const void* a_keys, const uint32_t* a_vals, int64_t n,
                    const void* b_keys, const uint32_t* b_vals, int64_t m,
@@ -136,16 +153,37 @@ TM_API tm_status tm_cross_ranks(tm_key_type kt,
                          const void* b_keys, int64_t m, int64_t p,
                          int64_t* xbar, int64_t* ybar, tm_stream_t stream);
 
-/* Steps 3 and 4 alone: given the cross ranks of tm_cross_ranks for the same
- * (A, B, p), merges the 2p subproblems into C.  `status` is a device int32
- * the kernel sets on a device-side error (not cleared here).  cfg->p is
- * ignored (p is the argument). */
-TM_API tm_status tm_merge_subproblems(tm_key_type kt,
-                               const void* a_keys, const uint32_t* a_vals, int64_t n,
-                               const void* b_keys, const uint32_t* b_vals, int64_t m,
-                               int64_t p, const int64_t* xbar, const int64_t* ybar,
-                               void* c_keys, uint32_t* c_vals, int32_t* status,
-                               const tm_config* cfg, tm_stream_t stream);
+/* Steps 3 and 4, first half (subproblem selection): for each of the 2p
+ * processing elements of tm_cross_ranks' (A, B, p) whose block is not empty,
+ * one tile record of tm_tile_record_bytes() bytes (device, 16-byte aligned):
+ * the subproblem's A range, B range and output offset, chosen by the five
+ * cases (a)-(e) of Step 3 and their mirror in Step 4.  Records are stored
+ * in merge-path order (by output offset), tm_plan_tile_count(n, m, p) of
+ * them; `tiles` must hold 2p records.  Layout of a record: int64 a0, b0, c0
+ * (first A index, first B index, first output index), int32 nA, nB. */
+TM_API size_t tm_tile_record_bytes(void);
+TM_API int64_t tm_plan_tile_count(int64_t n, int64_t m, int64_t p);
+TM_API tm_status tm_plan_subproblems(int64_t n, int64_t m, int64_t p,
+                                     const int64_t* xbar, const int64_t* ybar,
+                                     void* tiles, const tm_config* cfg, tm_stream_t stream);
+
+/* Largest subproblem of (n, m, p): ceil(n/p) + ceil(m/p) elements (each
+ * range lies inside one block of its array).  -1 on bad arguments. */
+TM_API int32_t tm_merge_tile_cap(int64_t n, int64_t m, int64_t p);
+
+/* Steps 3 and 4, second half (the stable merges): merges every tile record
+ * into C with the persistent staged tile-merge kernel.  Consecutive records
+ * (adjacent on the merge path) are packed into one staged tile while the
+ * total stays within `cap`, which must bound every single record
+ * (tm_merge_tile_cap).  `control` is a 256-byte device block: int32 status
+ * word at byte 0 (set on a device-side error, not cleared here), work-queue
+ * counter at byte 8 (reset by this call). */
+TM_API tm_status tm_merge_tiles(tm_key_type kt,
+                                const void* a_keys, const uint32_t* a_vals, int64_t n,
+                                const void* b_keys, const uint32_t* b_vals, int64_t m,
+                                const void* tiles, int64_t n_tiles, int32_t cap,
+                                void* c_keys, uint32_t* c_vals, void* control,
+                                const tm_config* cfg, tm_stream_t stream);
 
 /* The subproblems of Steps 3-4 as the device computes them: for k < p the
  * A-side processing element k, for k >= p the B-side one (k - p).  Row k of

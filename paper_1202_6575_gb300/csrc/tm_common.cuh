@@ -9,7 +9,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/tm.h"
+#include "tm.h"
 
 namespace pmerge {
 
@@ -51,9 +51,11 @@ __host__ __device__ __forceinline__ I block_of(I len, I p, I k) {
 }
 
 // Smallest block index j whose start y_j is >= k (0 <= k <= len): the block
-// of k, or the next one when k lies strictly inside its block.
+// of k, or the next one when k lies strictly inside its block.  For k = len
+// that is the first empty block (index len when len < p), else block p.
 template <typename I>
 __host__ __device__ __forceinline__ I first_block_at_or_after(I len, I p, I k) {
+    if (k >= len) return len < p ? len : p;
     I j = block_of(len, p, k);
     return (block_start(len, p, j) == k) ? j : j + 1;
 }

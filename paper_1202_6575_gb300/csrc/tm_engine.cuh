@@ -1,0 +1,545 @@
+// Persistent, warp-specialised tile-merge engine shared by the single merge,
+// the batched merge and the merge-sort passes.
+//
+// Work: a device array of tile descriptors, one per subproblem of Steps 3-4
+// (an A range, a B range and the output offset they define).  Plan kernels
+// write the descriptors; this kernel only moves and merges data.
+//
+// CTA = 1 producer warp + T consumer threads.
+//  producer: pulls descriptors from a device work queue (atomicAdd, a few
+//    tiles per grab), waits for a free input stage, writes the tile header,
+//    and issues the bulk copies (cp.async.bulk, TMA engine) of the tile's
+//    A keys, A payloads, B keys and B payloads on the stage's mbarrier.
+//  consumers: wait for a full stage, re-split the tile among themselves by
+//    the paper's rule (T blocks per piece, rank_low of each A-block start in
+//    the B piece, rank_high of each B-block start in the A piece, then the 2T
+//    sub-subproblems of the split-point form), merge serially into an output
+//    buffer, release the input stage, and store the output with bulk copies
+//    (16-byte aligned middle) plus plain stores for the ragged ends.
+// Input stages and output buffers are multi-buffered, so the loads of later
+// tiles and the stores of earlier ones overlap the merge of the current one.
+#pragma once
+
+#include "tm_common.cuh"
+
+namespace pmerge {
+
+// One subproblem: A[a0, a0+nA) and B[b0, b0+nB) merge into C[c0, c0+nA+nB).
+// Plan kernels write the records in merge-path (chain) order, so that
+// consecutive records are adjacent pieces of the merge path: their A ranges,
+// B ranges and outputs are contiguous, and any run of them is itself a valid
+// subproblem.
+struct __align__(16) TileDesc {
+    int64_t a0, b0, c0;
+    int32_t nA, nB;
+};
+static_assert(sizeof(TileDesc) == 32, "descriptor layout");
+
+// ceil(2^31 / d): floor(k / d) == (k * inv31(d)) >> 31 exactly for
+// 0 <= k < 2^15 and 1 <= d <= 2^14 (the error term k*(M - 2^31/d)/2^31 stays
+// below 2^-16 < 1/d).  Tiles hold at most 16386 elements, so every index
+// and divisor of the in-CTA block arithmetic is in range.
+__host__ __device__ __forceinline__ uint32_t inv31(uint32_t d) {
+    return d ? (uint32_t)(((1ull << 31) + d - 1) / d) : 0u;
+}
+__device__ __forceinline__ int div_inv31(int k, uint32_t m) {
+    return (int)(((uint64_t)(uint32_t)k * m) >> 31);
+}
+
+// The paper's block decomposition of `len` elements into T = 2^LOG_T blocks
+// (first r blocks one longer), with the block-of-index rule by inverses.
+template <int LOG_T>
+struct BlockSplit {
+    int len, q, r, head;
+    uint32_t m1, m0;   // inverses of q + 1 and q
+    __device__ __forceinline__ BlockSplit(int n, uint32_t inv_q1, uint32_t inv_q0)
+        : len(n), q(n >> LOG_T), r(n & ((1 << LOG_T) - 1)), head(r * ((n >> LOG_T) + 1)), m1(inv_q1), m0(inv_q0) {}
+    // x_i = i*q + min(i, r)  (= i*ceil for i < r, i*floor + r otherwise)
+    __device__ __forceinline__ int start(int i) const { return i * q + min(i, r); }
+    // block holding k (k = len -> T)
+    __device__ __forceinline__ int of(int k) const {
+        if (k >= len) return 1 << LOG_T;
+        return (k < head) ? div_inv31(k, m1) : div_inv31(k - head, m0) + r;
+    }
+    // first block whose start is >= k
+    __device__ __forceinline__ int first_at_or_after(int k) const {
+        int j = of(k);
+        return (start(j) == k) ? j : j + 1;
+    }
+};
+
+// Named barrier among the consumer warps only (the producer never joins).
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
+}
+
+// rank_low(x, X[0..len)) and rank_high(y, Y[0..len2)) in shared memory, as
+// two interleaved branch-free bisections (power-of-two steps).
+template <typename K>
+__device__ __forceinline__ void rank_pair_smem(const K* X, int lenX, K x, int& rlow,
+                                               const K* Y, int lenY, K y, int& rhigh) {
+    int lo = 0, hi = 0;
+    int mx = lenX > lenY ? lenX : lenY;
+    if (mx > 0) {
+        for (int step = 1 << (31 - __clz(mx)); step > 0; step >>= 1) {
+            int a = lo + step, b = hi + step;
+            if (a <= lenX && X[a - 1] < x) lo = a;
+            if (b <= lenY && !(y < Y[b - 1])) hi = b;
+        }
+    }
+    rlow = lo;
+    rhigh = hi;
+}
+
+// Serial stable merge of sA[ia0..ia1) and sB[ib0..ib1) into sC from ia0 + ib0
+// (B taken only when strictly smaller).  Reads at most one element past a
+// range end, which lies inside the padded stage region.
+template <typename K>
+__device__ __forceinline__ void merge_run(const K* sAk, const uint32_t* sAv, int ia0, int ia1,
+                                          const K* sBk, const uint32_t* sBv, int ib0, int ib1,
+                                          K* sCk, uint32_t* sCv) {
+    int i = ia0, j = ib0, o = ia0 + ib0;
+    const int oend = ia1 + ib1;
+    K ka = sAk[i];
+    K kb = sBk[j];
+#pragma unroll 2
+    for (; o < oend; ++o) {
+        const bool takeB = (j < ib1) && ((i >= ia1) || (kb < ka));
+        const int idx = takeB ? j : i;
+        const K* ks = takeB ? sBk : sAk;
+        const uint32_t* vs = takeB ? sBv : sAv;
+        sCk[o] = takeB ? kb : ka;
+        sCv[o] = vs[idx];
+        const K nxt = ks[idx + 1];
+        if (takeB) { kb = nxt; ++j; } else { ka = nxt; ++i; }
+    }
+}
+
+// Number of A elements among the first d outputs of the stable merge of
+// sA[0..nA) and sB[0..nB): by the position formulas of Section 2 that is the
+// i with B[d-i-1] < A[i] (A[i] lands at i + rank_low(A[i], B) >= d) and
+// A[i-1] <= B[d-i] (B[d-i] lands at d-i + rank_high(B[d-i], A) >= d).
+template <typename K>
+__device__ __forceinline__ int corank_smem(const K* sA, int nA, const K* sB, int nB, int d) {
+    int lo = d > nB ? d - nB : 0, hi = d < nA ? d : nA;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sB[d - mid - 1] < sA[mid]) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Stage layout
+// ---------------------------------------------------------------------------
+// Per input stage:  header (128 B) | keys region | payload region.
+// A piece at the start of a region, B piece at a 16-byte boundary after it;
+// each piece sits at the misalignment of its global source so that the
+// aligned middle is one bulk copy.  Per output buffer: keys | payloads, at
+// the misalignment of the global destination.
+
+struct EngineLayout {
+    uint32_t stage_bytes, keys_off, vals_off;   // within a stage
+    uint32_t out_bytes, out_vals_off;           // within an output buffer
+    uint32_t split_off, bars_off;               // xs/ys, mbarriers
+    uint32_t stages_off, outs_off, total;
+};
+
+__host__ __device__ inline uint32_t ru128(uint32_t x) { return (x + 127u) & ~127u; }
+
+__host__ __device__ inline EngineLayout make_engine_layout(int cap, int ksize, int T, int s_in, int s_out) {
+    EngineLayout L;
+    uint32_t kreg = ru128((uint32_t)cap * ksize + 96);
+    uint32_t vreg = ru128((uint32_t)cap * 4 + 96);
+    L.keys_off = 128;
+    L.vals_off = 128 + kreg;
+    L.stage_bytes = 128 + kreg + vreg;
+    L.out_vals_off = ru128((uint32_t)cap * ksize + 16);
+    L.out_bytes = L.out_vals_off + ru128((uint32_t)cap * 4 + 16);
+    L.bars_off = 0;                                   // 2 * s_in mbarriers (<= 128 B)
+    L.split_off = 128;
+    uint32_t o = 128 + ru128(8u * (T + 1));
+    L.stages_off = o;
+    o += (uint32_t)s_in * L.stage_bytes;
+    L.outs_off = o;
+    o += (uint32_t)s_out * L.out_bytes;
+    L.total = o;
+    return L;
+}
+
+// Header the producer writes into a stage (read by the consumers).
+struct StageHeader {
+    int64_t c0;
+    int32_t nA, nB;
+    uint32_t mA1, mA0, mB1, mB0;
+    uint32_t kA, kB, vA, vB;       // byte offsets of element 0 of each piece within its region
+    int32_t end;                   // 1: no more tiles
+};
+
+struct EngineArgs {
+    const TileDesc* desc;
+    int64_t n_items;
+    unsigned long long* queue;     // work-queue counter, zero at launch
+    int32_t* status;
+    const void* A; const uint32_t* Av; int64_t lenA;   // arrays the descriptors index
+    const void* B; const uint32_t* Bv; int64_t lenB;
+    void* C; uint32_t* Cv;
+    int cap;                       // max nA + nB of any tile
+    int grab;                      // records per queue grab (<= 32)
+    EngineLayout lay;
+};
+
+// Bulk-copy window of elements [lo, lo+cnt) of an array (base, len,
+// element size E) into a region at byte offset `dst_off`: the region
+// receives the 16-byte window starting at round_down(&X[lo], 16); the bytes
+// [t0, t1) inside the array's own aligned span go by bulk copy, anything of
+// [g0, g1) outside it (only next to the array's first or last 16 bytes) by
+// plain loads.  Pass 0 does the plain loads and returns the bulk bytes in
+// tx_bytes; pass 1 issues the bulk copy.  Returns the byte offset of X[lo]
+// within the region.
+__device__ __forceinline__ uint32_t stage_piece(uint8_t* region, uint32_t dst_off, const void* base,
+                                                int64_t len, int64_t lo, int64_t cnt, uint32_t E,
+                                                uint64_t* bar, uint32_t& tx_bytes, int pass) {
+    uintptr_t b = reinterpret_cast<uintptr_t>(base);
+    uintptr_t g0 = b + (uintptr_t)lo * E, g1 = g0 + (uintptr_t)cnt * E;
+    uintptr_t w0 = g0 & ~(uintptr_t)15;
+    uintptr_t lim0 = (b + 15) & ~(uintptr_t)15, lim1 = (b + (uintptr_t)len * E) & ~(uintptr_t)15;
+    uintptr_t t0 = w0 > lim0 ? w0 : lim0;
+    uintptr_t r1 = (g1 + 15) & ~(uintptr_t)15;
+    uintptr_t t1 = r1 < lim1 ? r1 : lim1;
+    uint8_t* dst = region + dst_off;
+    if (cnt > 0) {
+        if (t1 > t0) {
+            if (pass == 1) bulk_g2s(dst + (t0 - w0), reinterpret_cast<const void*>(t0), (uint32_t)(t1 - t0), bar);
+            else tx_bytes += (uint32_t)(t1 - t0);
+        } else {
+            t0 = t1 = g1;                         // no bulk part: all plain
+        }
+        if (pass == 0) {                          // plain loads of [g0, min(t0, g1)) and [max(t1, g0), g1)
+            for (uintptr_t a = g0; a < g1 && a < t0; a += E) {
+                if (E == 8) *reinterpret_cast<uint64_t*>(dst + (a - w0)) = *reinterpret_cast<const uint64_t*>(a);
+                else        *reinterpret_cast<uint32_t*>(dst + (a - w0)) = *reinterpret_cast<const uint32_t*>(a);
+            }
+            for (uintptr_t a = (t1 > g0 ? t1 : g0); a < g1; a += E) {
+                if (E == 8) *reinterpret_cast<uint64_t*>(dst + (a - w0)) = *reinterpret_cast<const uint64_t*>(a);
+                else        *reinterpret_cast<uint32_t*>(dst + (a - w0)) = *reinterpret_cast<const uint32_t*>(a);
+            }
+        }
+    }
+    return dst_off + (uint32_t)(g0 - w0);
+}
+
+// Output of L elements at C[c0..): bulk store of the aligned middle (one
+// thread) and plain stores of the ragged ends.  `buf` holds element 0 at
+// byte offset (destination address & 15).
+template <typename T>
+__device__ __forceinline__ void store_out(const uint8_t* buf, const void* base, int64_t c0, int L,
+                                          int tid, int nthreads, bool issuer) {
+    const uintptr_t E = sizeof(T);
+    uintptr_t g0 = reinterpret_cast<uintptr_t>(base) + (uintptr_t)c0 * E;
+    uintptr_t g1 = g0 + (uintptr_t)L * E;
+    uintptr_t m0 = (g0 + 15) & ~(uintptr_t)15, m1 = g1 & ~(uintptr_t)15;
+    const uint8_t* src0 = buf + (g0 & 15);              // element 0 in the buffer
+    if (m1 > m0) {
+        if (issuer) bulk_s2g(reinterpret_cast<void*>(m0), src0 + (m0 - g0), (uint32_t)(m1 - m0));
+        int nh = (int)((m0 - g0) / E), t0 = (int)((m1 - g0) / E);
+        if (tid < nh) reinterpret_cast<T*>(g0)[tid] = reinterpret_cast<const T*>(src0)[tid];
+        int e = t0 + tid;
+        if (e < L) reinterpret_cast<T*>(g0)[e] = reinterpret_cast<const T*>(src0)[e];
+    } else {
+        for (int e = tid; e < L; e += nthreads) reinterpret_cast<T*>(g0)[e] = reinterpret_cast<const T*>(src0)[e];
+    }
+}
+
+// In-CTA split of a staged tile among the consumer threads:
+//   kSplitBlocks   - the paper's rule again: T blocks per piece, cross ranks
+//                    of the block starts, 2T sub-subproblems, two per thread,
+//                    merged into a separate output buffer;
+//   kSplitDiagonal - equal output runs of VT elements (VT odd): thread t
+//                    starts at the co-rank of output diagonal t*VT (the
+//                    position formulas of Section 2) and merges VT elements
+//                    into registers; the runs are then written back into the
+//                    consumed input stage (odd VT: bank-conflict free) and
+//                    stored from there.
+enum { kSplitBlocks = 0, kSplitDiagonal = 1 };
+
+// Producer warp: pulls tile records from the work queue and stages them.
+// A grab of G consecutive records is packed greedily into tiles of at most
+// `cap` elements (consecutive records are adjacent on the merge path).
+// Lanes 0..3 handle the four pieces (A keys, A payloads, B keys, B payloads)
+// in parallel; lane 0 writes the header and arms the stage's barrier.
+template <typename K, int LOG_T, int S_IN, int SPLIT>
+__device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* smem, uint64_t* full,
+                                                uint64_t* empty, int lane) {
+    int k = 0;                                        // fills issued
+    bool ok = true;
+    const int G = g.grab;
+    const unsigned long long nitems = (unsigned long long)g.n_items;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(g.queue, (unsigned long long)G);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    TileDesc d{};
+    if (lane < G && base + lane < nitems) d = g.desc[base + lane];
+    while (ok && base < nitems) {
+        unsigned long long nbase = 0;                 // prefetch the next grab
+        if (lane == 0) nbase = atomicAdd(g.queue, (unsigned long long)G);
+        nbase = __shfl_sync(0xffffffffu, nbase, 0);
+        TileDesc nd{};
+        if (lane < G && nbase + lane < nitems) nd = g.desc[nbase + lane];
+        const int avail = (int)min((unsigned long long)G, nitems - base);
+        for (int q = 0; q < avail && ok;) {
+            const int64_t a0 = __shfl_sync(0xffffffffu, d.a0, q);
+            const int64_t b0 = __shfl_sync(0xffffffffu, d.b0, q);
+            const int64_t c0 = __shfl_sync(0xffffffffu, d.c0, q);
+            int nA = __shfl_sync(0xffffffffu, d.nA, q);
+            int nB = __shfl_sync(0xffffffffu, d.nB, q);
+            ++q;
+            for (; q < avail; ++q) {                  // pack the following records while they fit
+                const int xA = __shfl_sync(0xffffffffu, d.nA, q);
+                const int xB = __shfl_sync(0xffffffffu, d.nB, q);
+                if (nA + nB + xA + xB > g.cap) break;
+                nA += xA;
+                nB += xB;
+            }
+            if (nA + nB == 0) continue;
+            if (nA < 0 || nB < 0 || nA + nB > g.cap) {
+                if (lane == 0) set_status(g.status, TM_ERR_BOUNDS);
+                continue;
+            }
+            const int s = k % S_IN;
+            int free_ok = 1;
+            if (lane == 0 && k >= S_IN)
+                free_ok = mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, kWaitLimitNs) ? 1 : 0;
+            free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+            if (!free_ok) {
+                if (lane == 0) set_status(g.status, TM_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
+            // piece of this lane: 0 A keys, 1 A payloads, 2 B keys, 3 B payloads
+            const bool isB = lane >= 2, isV = (lane & 1) != 0;
+            const uint32_t E = isV ? 4u : (uint32_t)sizeof(K);
+            const void* pbase = isB ? (isV ? (const void*)g.Bv : g.B) : (isV ? (const void*)g.Av : g.A);
+            const int64_t plen = isB ? g.lenB : g.lenA, plo = isB ? b0 : a0, pcnt = isB ? nB : nA;
+            uint8_t* region = st + (isV ? g.lay.vals_off : g.lay.keys_off);
+            uint32_t dst_off = 0;
+            if (isB) {   // after the A piece of the same region, on a 16-byte boundary
+                const uintptr_t abase = reinterpret_cast<uintptr_t>(isV ? (const void*)g.Av : g.A);
+                const uint32_t aoff = (uint32_t)((abase + (uintptr_t)a0 * E) & 15);
+                dst_off = (aoff + (uint32_t)nA * E + 31u) & ~15u;
+            }
+            uint32_t tx = 0, off = 0, inv = 0;
+            if (lane < 4) {
+                off = stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], tx, 0);
+                if (SPLIT == kSplitBlocks) {          // inverses of q+1 and q per piece length
+                    const uint32_t qn = (uint32_t)(isB ? nB : nA) >> LOG_T;
+                    inv = inv31(isV ? qn : qn + 1);
+                }
+            }
+            tx += __shfl_xor_sync(0xffffffffu, tx, 1);
+            tx += __shfl_xor_sync(0xffffffffu, tx, 2);
+            const uint32_t oKA = __shfl_sync(0xffffffffu, off, 0), oVA = __shfl_sync(0xffffffffu, off, 1);
+            const uint32_t oKB = __shfl_sync(0xffffffffu, off, 2), oVB = __shfl_sync(0xffffffffu, off, 3);
+            const uint32_t mA1 = __shfl_sync(0xffffffffu, inv, 0), mA0 = __shfl_sync(0xffffffffu, inv, 1);
+            const uint32_t mB1 = __shfl_sync(0xffffffffu, inv, 2), mB0 = __shfl_sync(0xffffffffu, inv, 3);
+            __syncwarp();                              // plain edge loads before the arrive
+            if (lane == 0) {
+                StageHeader* h = reinterpret_cast<StageHeader*>(st);
+                h->c0 = c0; h->nA = nA; h->nB = nB;
+                h->mA1 = mA1; h->mA0 = mA0; h->mB1 = mB1; h->mB0 = mB0;
+                h->kA = oKA; h->vA = oVA; h->kB = oKB; h->vB = oVB;
+                h->end = 0;
+                mbar_arrive_expect_tx(&full[s], tx);
+            }
+            __syncwarp();
+            uint32_t unused = 0;
+            if (lane < 4) stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], unused, 1);
+            ++k;
+        }
+        base = nbase;
+        d = nd;
+    }
+    if (lane == 0 && ok) {                            // end marker for the consumers
+        const int s = k % S_IN;
+        if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, kWaitLimitNs)) {
+            set_status(g.status, TM_ERR_TIMEOUT);
+        } else {
+            StageHeader* h = reinterpret_cast<StageHeader*>(smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes);
+            h->end = 1;
+            mbar_arrive_expect_tx(&full[s], 0);
+        }
+    }
+}
+
+// Consumers, paper's rule inside the CTA (output via separate buffers).
+template <typename K, int LOG_T, int S_IN, int S_OUT>
+__device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uint8_t* smem, uint64_t* full,
+                                                        uint64_t* empty, int tid) {
+    constexpr int T = 1 << LOG_T;
+    int* xs = reinterpret_cast<int*>(smem + g.lay.split_off);
+    int* ys = xs + (T + 1);
+    const bool leader = (tid == 0);
+    for (int k = 0;; ++k) {
+        const int s = k % S_IN;
+        const int ob = k % S_OUT;
+        uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
+        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, kWaitLimitNs)) {
+            if (leader) set_status(g.status, TM_ERR_TIMEOUT);
+            break;
+        }
+        const StageHeader* h = reinterpret_cast<const StageHeader*>(st);
+        if (h->end) break;
+        const int nA = h->nA, nB = h->nB;
+        const int64_t c0 = h->c0;
+        const K* kA = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kA);
+        const K* kB = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kB);
+        const uint32_t* vA = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vA);
+        const uint32_t* vB = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vB);
+        const BlockSplit<LOG_T> SA(nA, h->mA1, h->mA0), SB(nB, h->mB1, h->mB0);
+        uint8_t* ob_base = smem + g.lay.outs_off + (uint32_t)ob * g.lay.out_bytes;
+        const uintptr_t gk = reinterpret_cast<uintptr_t>(g.C) + (uintptr_t)c0 * sizeof(K);
+        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * 4;
+        K* oK = reinterpret_cast<K*>(ob_base + (gk & 15));
+        uint32_t* oV = reinterpret_cast<uint32_t*>(ob_base + g.lay.out_vals_off + (gv & 15));
+
+        // Steps 1-2 inside the tile
+        {
+            const int xa = SA.start(tid), yb = SB.start(tid);
+            const K kx = kA[xa < nA ? xa : 0];
+            const K ky = kB[yb < nB ? yb : 0];
+            int rl, rh;
+            rank_pair_smem(kB, nB, kx, rl, kA, nA, ky, rh);
+            xs[tid] = (xa < nA) ? rl : nB;
+            ys[tid] = (yb < nB) ? rh : nA;
+            if (tid == 0) { xs[T] = nB; ys[T] = nA; }
+        }
+        if (leader && k >= S_OUT) bulk_wait_read<S_OUT - 1>();   // output buffer ob is free again
+        consumer_sync(T);
+        // Steps 3-4 inside the tile: A-side item tid, then B-side item tid
+        {
+            const int xa = SA.start(tid), xa1 = SA.start(tid + 1);
+            const int xb = xs[tid], xb1 = xs[tid + 1];
+            const int jn = SB.first_at_or_after(xb);
+            const int yjn = SB.start(jn);
+            int a1, b1;
+            if (jn < T && yjn < xb1) { a1 = ys[jn]; b1 = yjn; } else { a1 = xa1; b1 = xb1; }
+            merge_run(kA, vA, xa, a1, kB, vB, xb, b1, oK, oV);
+        }
+        {
+            const int yb = SB.start(tid), yb1s = SB.start(tid + 1);
+            const int ya = ys[tid], ya1 = ys[tid + 1];
+            const int in = SA.first_at_or_after(ya);
+            const int xin = SA.start(in);
+            int a1, b1;
+            if (in < T && xin < ya1) { b1 = xs[in]; a1 = xin; } else { b1 = yb1s; a1 = ya1; }
+            merge_run(kA, vA, ya, a1, kB, vB, yb, b1, oK, oV);
+        }
+        fence_proxy_async_smem();
+        consumer_sync(T);
+        if (leader) mbar_arrive_expect_tx(&empty[s], 0);         // input stage s may be refilled
+        const int L = nA + nB;
+        store_out<K>(ob_base, g.C, c0, L, tid, T, leader);
+        store_out<uint32_t>(ob_base + g.lay.out_vals_off, g.Cv, c0, L, tid, T, leader);
+        if (leader) bulk_commit();
+    }
+    if (leader) bulk_wait_read<0>();
+}
+
+// Consumers, equal output runs of VT elements per thread, results written
+// back into the consumed stage.  The stage is released one tile later, once
+// its bulk store has read it.
+template <typename K, int LOG_T, int S_IN, int VT>
+__device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, uint8_t* smem, uint64_t* full,
+                                                          uint64_t* empty, int tid) {
+    constexpr int T = 1 << LOG_T;
+    const bool leader = (tid == 0);
+    int pending = -1;                                  // stage whose store is still reading it
+    for (int k = 0;; ++k) {
+        const int s = k % S_IN;
+        uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
+        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, kWaitLimitNs)) {
+            if (leader) set_status(g.status, TM_ERR_TIMEOUT);
+            break;
+        }
+        const StageHeader* h = reinterpret_cast<const StageHeader*>(st);
+        if (h->end) break;
+        const int nA = h->nA, nB = h->nB;
+        const int64_t c0 = h->c0;
+        const K* kA = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kA);
+        const K* kB = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kB);
+        const uint32_t* vA = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vA);
+        const uint32_t* vB = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vB);
+        const int L = nA + nB;
+        const int d0 = tid * VT;
+        const int cnt = max(0, min(VT, L - d0));
+        K rk[VT];
+        uint32_t rv[VT];
+        if (cnt > 0) {
+            int i = corank_smem(kA, nA, kB, nB, d0);
+            int j = d0 - i;
+            K ka = kA[i], kb = kB[j];
+#pragma unroll
+            for (int q = 0; q < VT; ++q) {
+                if (q < cnt) {
+                    const bool takeB = (j < nB) && ((i >= nA) || (kb < ka));
+                    const int idx = takeB ? j : i;
+                    const K* ks = takeB ? kB : kA;
+                    const uint32_t* vs = takeB ? vB : vA;
+                    rk[q] = takeB ? kb : ka;
+                    rv[q] = vs[idx];
+                    const K nxt = ks[idx + 1];
+                    if (takeB) { kb = nxt; ++j; } else { ka = nxt; ++i; }
+                }
+            }
+        }
+        consumer_sync(T);                              // all reads of the stage's input done
+        const uintptr_t gk = reinterpret_cast<uintptr_t>(g.C) + (uintptr_t)c0 * sizeof(K);
+        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * 4;
+        uint8_t* bk = st + g.lay.keys_off;
+        uint8_t* bv = st + g.lay.vals_off;
+        K* oK = reinterpret_cast<K*>(bk + (gk & 15));
+        uint32_t* oV = reinterpret_cast<uint32_t*>(bv + (gv & 15));
+#pragma unroll
+        for (int q = 0; q < VT; ++q) {
+            if (q < cnt) { oK[d0 + q] = rk[q]; oV[d0 + q] = rv[q]; }
+        }
+        fence_proxy_async_smem();
+        consumer_sync(T);
+        store_out<K>(bk, g.C, c0, L, tid, T, leader);
+        store_out<uint32_t>(bv, g.Cv, c0, L, tid, T, leader);
+        if (leader) {
+            bulk_commit();
+            if (pending >= 0) {                         // previous tile's store has read its stage
+                bulk_wait_read<1>();
+                mbar_arrive_expect_tx(&empty[pending], 0);
+            }
+            pending = s;
+        }
+    }
+    if (leader) bulk_wait_read<0>();
+}
+
+template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT>
+__global__ void __launch_bounds__((1 << LOG_T) + 32)
+merge_engine_kernel(const EngineArgs g) {
+    constexpr int T = 1 << LOG_T;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + g.lay.bars_off);
+    uint64_t* empty = full + S_IN;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < S_IN; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (tid >= T) {
+        engine_producer<K, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
+        return;
+    }
+    if constexpr (SPLIT == kSplitDiagonal) engine_consumers_diagonal<K, LOG_T, S_IN, VT>(g, smem, full, empty, tid);
+    else                                   engine_consumers_blocks<K, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
+}
+
+}  // namespace pmerge

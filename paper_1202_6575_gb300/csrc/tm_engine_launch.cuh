@@ -1,0 +1,108 @@
+// Host-side launch of the persistent tile engine: picks the pipeline depth
+// (input stages, output buffers) and the grid from the tile capacity, the
+// key size and the device's shared memory.  Instantiated once per key type
+// in tm_engine_<type>.cu so the key types compile in parallel.
+#pragma once
+
+#include "tm_engine.cuh"
+#include "tm_host.h"
+
+namespace pmerge {
+
+template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT>
+tm_status launch_engine_s(const EngineArgs& a_in, const tm_config* cfg, cudaStream_t s) {
+    EngineArgs a = a_in;
+    a.lay = make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, S_IN, S_OUT);
+    auto kern = merge_engine_kernel<K, LOG_T, S_IN, S_OUT, SPLIT, VT>;
+    if (!ensure_smem_limit(kern, a.lay.total)) return TM_ERR_UNSUPPORTED;
+    const int block = (1 << LOG_T) + 32;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, a.lay.total) != cudaSuccess || per_sm < 1)
+        return TM_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)per_sm * sm_count();
+    if (cfg && cfg->grid > 0) grid = cfg->grid;
+    int64_t g = a.n_items / (grid * 8);
+    a.grab = (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
+    int64_t need = (a.n_items + a.grab - 1) / a.grab;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return TM_ERR_CUDA;
+    kern<<<(unsigned)grid, block, a.lay.total, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+// Paper's rule inside the CTA, with separate output buffers.  cfg->stages:
+// 4, 2 or 1 input stages; 0 picks 2 (1 when two do not fit).
+template <typename K, int LOG_T>
+tm_status launch_blocks(const EngineArgs& a, const tm_config* cfg, cudaStream_t s) {
+    const int want = (cfg && cfg->stages > 0) ? cfg->stages : 0;
+    switch (want) {
+        case 4: return launch_engine_s<K, LOG_T, 4, 2, kSplitBlocks, 1>(a, cfg, s);
+        case 2: return launch_engine_s<K, LOG_T, 2, 2, kSplitBlocks, 1>(a, cfg, s);
+        case 1: return launch_engine_s<K, LOG_T, 1, 1, kSplitBlocks, 1>(a, cfg, s);
+        case 0: break;
+        default: return TM_ERR_UNSUPPORTED;
+    }
+    if (make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, 2, 2).total <= device_smem_limit())
+        return launch_engine_s<K, LOG_T, 2, 2, kSplitBlocks, 1>(a, cfg, s);
+    return launch_engine_s<K, LOG_T, 1, 1, kSplitBlocks, 1>(a, cfg, s);
+}
+
+// Equal output runs of VT elements per thread, output written back into the
+// consumed stage (no output buffers).  A stage stays busy until the next
+// tile is merged, so at least 2 stages; cfg->stages 2, 3 or 4; default 4
+// when two such CTAs share an SM, else 3, else 2.
+template <typename K, int LOG_T, int VT>
+tm_status launch_diagonal_vt(const EngineArgs& a, const tm_config* cfg, cudaStream_t s) {
+    const int want = (cfg && cfg->stages > 0) ? cfg->stages : 0;
+    switch (want) {
+        case 4: return launch_engine_s<K, LOG_T, 4, 0, kSplitDiagonal, VT>(a, cfg, s);
+        case 3: return launch_engine_s<K, LOG_T, 3, 0, kSplitDiagonal, VT>(a, cfg, s);
+        case 2: return launch_engine_s<K, LOG_T, 2, 0, kSplitDiagonal, VT>(a, cfg, s);
+        case 0: break;
+        default: return TM_ERR_UNSUPPORTED;
+    }
+    const uint32_t lim = device_smem_limit();
+    const uint32_t half = lim / 2 > 2048 ? lim / 2 - 2048 : 0;
+    if (make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, 4, 0).total <= half)
+        return launch_engine_s<K, LOG_T, 4, 0, kSplitDiagonal, VT>(a, cfg, s);
+    if (make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, 3, 0).total <= lim)
+        return launch_engine_s<K, LOG_T, 3, 0, kSplitDiagonal, VT>(a, cfg, s);
+    return launch_engine_s<K, LOG_T, 2, 0, kSplitDiagonal, VT>(a, cfg, s);
+}
+
+// Smallest odd run length VT in {9, 17, 33} with T * VT >= cap.
+template <typename K, int LOG_T>
+tm_status launch_diagonal(const EngineArgs& a, const tm_config* cfg, cudaStream_t s) {
+    const int T = 1 << LOG_T;
+    if (a.cap <= 9 * T) return launch_diagonal_vt<K, LOG_T, 9>(a, cfg, s);
+    if (a.cap <= 17 * T) return launch_diagonal_vt<K, LOG_T, 17>(a, cfg, s);
+    if (a.cap <= 33 * T) return launch_diagonal_vt<K, LOG_T, 33>(a, cfg, s);
+    return TM_ERR_UNSUPPORTED;
+}
+
+template <typename K>
+tm_status launch_engine(const EngineArgs& a, const tm_config* cfg, cudaStream_t s) {
+    if (a.cap < 1 || a.cap > kMaxTileElems) return TM_ERR_UNSUPPORTED;
+    const int split = (cfg && cfg->split) ? cfg->split : TM_SPLIT_DEFAULT;
+    const int lt = log2_threads(cfg);
+    if (split == TM_SPLIT_BLOCKS) {
+        switch (lt) {
+            case 7: return launch_blocks<K, 7>(a, cfg, s);
+            case 8: return launch_blocks<K, 8>(a, cfg, s);
+            case 9: return launch_blocks<K, 9>(a, cfg, s);
+        }
+    } else if (split == TM_SPLIT_DIAGONAL) {
+        // tiles longer than 33 runs per thread fall back to the paper's rule
+        if (lt == 7 && a.cap <= 33 * 128) return launch_diagonal<K, 7>(a, cfg, s);
+        if (lt == 8 && a.cap <= 33 * 256) return launch_diagonal<K, 8>(a, cfg, s);
+        switch (lt) {
+            case 7: return launch_blocks<K, 7>(a, cfg, s);
+            case 8: return launch_blocks<K, 8>(a, cfg, s);
+            case 9: return launch_blocks<K, 9>(a, cfg, s);
+        }
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+}  // namespace pmerge

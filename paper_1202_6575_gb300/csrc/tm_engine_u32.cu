@@ -1,0 +1,6 @@
+// Persistent tile-engine kernels for uint32_t keys.
+#include "tm_engine_launch.cuh"
+
+namespace pmerge {
+template tm_status launch_engine<uint32_t>(const EngineArgs&, const tm_config*, cudaStream_t);
+}  // namespace pmerge

@@ -4,16 +4,17 @@
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
+#include <unordered_map>
 
 #include <cuda_runtime.h>
 
-#include "../../include/tm.h"
+#include "tm.h"
 
 namespace pmerge {
 
 constexpr int kVersion = 1;
-constexpr int kDefaultTile = 4096;        // elements of one staged subproblem
-constexpr int kDefaultThreads = 256;      // threads per tile-merge CTA
+constexpr int kDefaultTile = 2048;        // elements of one staged tile
+constexpr int kDefaultThreads = 128;      // consumer threads per tile-merge CTA
 constexpr int kMaxThreads = 512;          // launch bound of the tile kernels
 constexpr int kMaxTileElems = 16384;      // cap on capA + capB
 constexpr size_t kStatusBytes = 256;      // status word + padding at the head of a workspace
@@ -34,25 +35,24 @@ inline uint32_t device_smem_limit() {
     return (uint32_t)v < kMaxSmemBytes ? (uint32_t)v : kMaxSmemBytes;
 }
 
-// Raises a kernel's dynamic shared-memory limit to `bytes` (once per device
-// and kernel, to the device's maximum); false if `bytes` does not fit.
+// Raises a kernel's dynamic shared-memory limit to the device maximum (once
+// per kernel and device); false if `bytes` does not fit.
 template <typename Kernel>
 inline bool ensure_smem_limit(Kernel kernel, uint32_t bytes) {
     static std::mutex mu;
-    static uint64_t done_mask = 0;
-    static uint32_t limit[64] = {0};
+    static std::unordered_map<const void*, uint64_t> done;   // kernel -> device mask
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    const uint32_t lim = device_smem_limit();
+    if (lim == 0 || bytes > lim) return false;
     std::lock_guard<std::mutex> lock(mu);
-    if (!((done_mask >> dev) & 1ull)) {
-        uint32_t lim = device_smem_limit();
-        if (lim == 0) return false;
+    uint64_t& mask = done[reinterpret_cast<const void*>(kernel)];
+    if (!((mask >> dev) & 1ull)) {
         if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
             return false;
-        limit[dev] = lim;
-        done_mask |= 1ull << dev;
+        mask |= 1ull << dev;
     }
-    return bytes <= limit[dev];
+    return true;
 }
 
 // Streaming multiprocessors of the current device (cached per device).
@@ -72,5 +72,11 @@ inline int sm_count() {
 int64_t choose_blocks(int64_t n, int64_t m, const tm_config* cfg);
 int choose_threads(const tm_config* cfg);
 size_t merge_workspace_bytes(int64_t p);
+int log2_threads(const tm_config* cfg);
+tm_status merge_tiles_dispatch(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
+                               const void* b_keys, const uint32_t* b_vals, int64_t m,
+                               const void* tiles, int64_t n_tiles, int cap,
+                               void* c_keys, uint32_t* c_vals, void* control,
+                               const tm_config* cfg, cudaStream_t s);
 
 }  // namespace pmerge

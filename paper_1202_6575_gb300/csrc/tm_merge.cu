@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "tm_engine.cuh"
 #include "tm_host.h"
 #include "tm_tile.cuh"
 
@@ -58,8 +59,37 @@ subproblem_table_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restri
     table[4 * k + 2] = b0; table[4 * k + 3] = b1;
 }
 
+// Steps 3-4 planning: one thread per processing element writes the tile
+// record of its subproblem (the split-point form of the five cases) at the
+// subproblem's place on the merge path.  A point P_A(i) = (x_i, xbar_i) has
+// i A-points and first_block_at_or_after(m, p, xbar_i) B-points before it
+// (B block j starts before A[x_i] iff y_j < xbar_i), and symmetrically for
+// P_B(j); so the chain index is a sum of two O(1) terms.  Empty blocks (when
+// p exceeds a length) have empty subproblems and write nothing; the
+// non-empty records fill indices [0, min(p, n) + min(p, m)).
+__global__ void __launch_bounds__(256)
+plan_single_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restrict__ xbar,
+                   const int64_t* __restrict__ ybar, TileDesc* __restrict__ desc) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * p) return;
+    const bool a_side = k < p;
+    const int64_t pe = a_side ? k : k - p;
+    if (a_side ? block_start<int64_t>(n, p, pe) >= n : block_start<int64_t>(m, p, pe) >= m) return;
+    auto xb = [&](int64_t i) { return __ldg(xbar + i); };
+    auto yb = [&](int64_t j) { return __ldg(ybar + j); };
+    int64_t a0, a1, b0, b1;
+    subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
+    const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
+                                 : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
+    TileDesc d;
+    d.a0 = a0; d.b0 = b0; d.c0 = a0 + b0;
+    d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);
+    desc[chain] = d;
+}
+
 // ---------------------------------------------------------------------------
-// Steps 3-4: one CTA per subproblem
+// Steps 3-4 without the planning pass: one CTA per subproblem (used by the
+// allocation-free entry point, whose scratch holds only the cross ranks)
 // ---------------------------------------------------------------------------
 
 template <typename K>
@@ -201,27 +231,111 @@ static tm_status launch_cross_ranks(const K* A, int64_t n, const K* B, int64_t m
     return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
 }
 
-size_t merge_workspace_bytes(int64_t p) {
-    return kStatusBytes + 2 * align_up((size_t)(p + 1) * sizeof(int64_t), 256);
+// ---------------------------------------------------------------------------
+// Persistent tile engine launch
+// ---------------------------------------------------------------------------
+
+int log2_threads(const tm_config* cfg) {
+    const int T = choose_threads(cfg);
+    return T == 128 ? 7 : (T == 256 ? 8 : (T == 512 ? 9 : -1));
 }
 
+// Instantiated per key type in tm_engine_<type>.cu.
 template <typename K>
-static tm_status merge_typed(const void* a_keys, const uint32_t* a_vals, int64_t n,
+tm_status launch_engine(const EngineArgs& a, const tm_config* cfg, cudaStream_t s);
+extern template tm_status launch_engine<uint32_t>(const EngineArgs&, const tm_config*, cudaStream_t);
+extern template tm_status launch_engine<int32_t>(const EngineArgs&, const tm_config*, cudaStream_t);
+extern template tm_status launch_engine<uint64_t>(const EngineArgs&, const tm_config*, cudaStream_t);
+extern template tm_status launch_engine<float>(const EngineArgs&, const tm_config*, cudaStream_t);
+
+template <typename K>
+static tm_status merge_tiles_typed(const void* a_keys, const uint32_t* a_vals, int64_t n,
+                                   const void* b_keys, const uint32_t* b_vals, int64_t m,
+                                   const TileDesc* tiles, int64_t n_tiles, int cap,
+                                   void* c_keys, uint32_t* c_vals, void* control,
+                                   const tm_config* cfg, cudaStream_t s) {
+    EngineArgs a{};
+    a.desc = tiles; a.n_items = n_tiles;
+    a.status = reinterpret_cast<int32_t*>(control);
+    a.queue = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(control) + 8);
+    a.A = a_keys; a.Av = a_vals; a.lenA = n;
+    a.B = b_keys; a.Bv = b_vals; a.lenB = m;
+    a.C = c_keys; a.Cv = c_vals;
+    a.cap = cap;
+    return launch_engine<K>(a, cfg, s);
+}
+
+tm_status merge_tiles_dispatch(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
+                               const void* b_keys, const uint32_t* b_vals, int64_t m,
+                               const void* tiles, int64_t n_tiles, int cap,
+                               void* c_keys, uint32_t* c_vals, void* control,
+                               const tm_config* cfg, cudaStream_t s) {
+    const TileDesc* t = static_cast<const TileDesc*>(tiles);
+    switch (kt) {
+        case TM_KEY_U32: return merge_tiles_typed<uint32_t>(a_keys, a_vals, n, b_keys, b_vals, m, t, n_tiles, cap, c_keys, c_vals, control, cfg, s);
+        case TM_KEY_I32: return merge_tiles_typed<int32_t>(a_keys, a_vals, n, b_keys, b_vals, m, t, n_tiles, cap, c_keys, c_vals, control, cfg, s);
+        case TM_KEY_U64: return merge_tiles_typed<uint64_t>(a_keys, a_vals, n, b_keys, b_vals, m, t, n_tiles, cap, c_keys, c_vals, control, cfg, s);
+        case TM_KEY_F32: return merge_tiles_typed<float>(a_keys, a_vals, n, b_keys, b_vals, m, t, n_tiles, cap, c_keys, c_vals, control, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+static tm_status launch_plan_single(int64_t n, int64_t m, int64_t p, const int64_t* xbar, const int64_t* ybar,
+                                    TileDesc* desc, cudaStream_t s) {
+    int64_t blocks = (2 * p + 255) / 256;
+    if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    plan_single_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, m, p, xbar, ybar, desc);
+    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+// Largest subproblem of the single merge: one A-block piece plus one B-block
+// piece (Section 2: the ranges of cases (a)-(e) lie inside blocks).
+static int64_t single_merge_cap(int64_t n, int64_t m, int64_t p) {
+    return ceil_div64(n, p) + ceil_div64(m, p);
+}
+
+// Non-empty subproblems: one per non-empty block of either array.
+static int64_t single_merge_tiles(int64_t n, int64_t m, int64_t p) {
+    return (n < p ? n : p) + (m < p ? m : p);
+}
+
+// Workspace of tm_merge: [status int32 | queue u64 | pad to 256] xbar ybar tiles.
+struct MergeWs { int32_t* status; void* control; int64_t* xbar; int64_t* ybar; TileDesc* tiles; size_t bytes; };
+
+static MergeWs merge_ws_layout(void* base, int64_t p) {
+    MergeWs w;
+    uint8_t* b = static_cast<uint8_t*>(base);
+    size_t o = kStatusBytes;
+    w.status = reinterpret_cast<int32_t*>(b);
+    w.control = b;
+    w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(p + 1) * 8, 256);
+    w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(p + 1) * 8, 256);
+    w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)(2 * p) * sizeof(TileDesc), 256);
+    w.bytes = o;
+    return w;
+}
+
+size_t merge_workspace_bytes(int64_t p) { return merge_ws_layout(nullptr, p).bytes; }
+
+template <typename K>
+static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
                              const void* b_keys, const uint32_t* b_vals, int64_t m,
                              void* c_keys, uint32_t* c_vals, void* ws, int64_t p,
                              const tm_config* cfg, cudaStream_t s) {
-    uint8_t* w = static_cast<uint8_t*>(ws);
-    int32_t* status = reinterpret_cast<int32_t*>(w);
-    int64_t* xbar = reinterpret_cast<int64_t*>(w + kStatusBytes);
-    int64_t* ybar = reinterpret_cast<int64_t*>(w + kStatusBytes + align_up((size_t)(p + 1) * 8, 256));
-    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    MergeWs w = merge_ws_layout(ws, p);
+    if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
     if (n + m == 0) return TM_OK;
+    if (log2_threads(cfg) < 0) return TM_ERR_UNSUPPORTED;
+    const int64_t cap = single_merge_cap(n, m, p);
+    if (cap > kMaxTileElems) return TM_ERR_UNSUPPORTED;
     const K* A = static_cast<const K*>(a_keys);
     const K* B = static_cast<const K*>(b_keys);
-    tm_status st = launch_cross_ranks<K>(A, n, B, m, p, xbar, ybar, s);
+    tm_status st = launch_cross_ranks<K>(A, n, B, m, p, w.xbar, w.ybar, s);
     if (st != TM_OK) return st;
-    return launch_tile_merge<K>(A, a_vals, n, B, b_vals, m, p, xbar, ybar,
-                                static_cast<K*>(c_keys), c_vals, status, cfg, s);
+    st = launch_plan_single(n, m, p, w.xbar, w.ybar, w.tiles, s);
+    if (st != TM_OK) return st;
+    return merge_tiles_dispatch(kt, a_keys, a_vals, n, b_keys, b_vals, m, w.tiles, single_merge_tiles(n, m, p),
+                                (int)cap, c_keys, c_vals, w.control, cfg, s);
 }
 
 }  // namespace pmerge
@@ -282,10 +396,10 @@ tm_status tm_merge(tm_key_type kt,
         return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (kt) {
-        case TM_KEY_U32: return merge_typed<uint32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
-        case TM_KEY_I32: return merge_typed<int32_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
-        case TM_KEY_U64: return merge_typed<uint64_t>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
-        case TM_KEY_F32: return merge_typed<float>(a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_U32: return merge_typed<uint32_t>(kt, a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_I32: return merge_typed<int32_t>(kt, a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_U64: return merge_typed<uint64_t>(kt, a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
+        case TM_KEY_F32: return merge_typed<float>(kt, a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);
     }
     return TM_ERR_UNSUPPORTED;
 }
@@ -309,28 +423,45 @@ tm_status tm_cross_ranks(tm_key_type kt, const void* a_keys, int64_t n,
     return TM_ERR_UNSUPPORTED;
 }
 
-tm_status tm_merge_subproblems(tm_key_type kt,
-                               const void* a_keys, const uint32_t* a_vals, int64_t n,
-                               const void* b_keys, const uint32_t* b_vals, int64_t m,
-                               int64_t p, const int64_t* xbar, const int64_t* ybar,
-                               void* c_keys, uint32_t* c_vals, int32_t* status,
-                               const tm_config* cfg, tm_stream_t stream) {
-    if (n < 0 || m < 0 || p < 1 || !xbar || !ybar) return TM_ERR_INVALID;
+size_t tm_tile_record_bytes(void) { return sizeof(TileDesc); }
+
+int32_t tm_merge_tile_cap(int64_t n, int64_t m, int64_t p) {
+    if (n < 0 || m < 0 || p < 1) return -1;
+    int64_t c = single_merge_cap(n, m, p);
+    return c > 0x7fffffff ? -1 : (int32_t)c;
+}
+
+int64_t tm_plan_tile_count(int64_t n, int64_t m, int64_t p) {
+    if (n < 0 || m < 0 || p < 1) return -1;
+    return single_merge_tiles(n, m, p);
+}
+
+tm_status tm_plan_subproblems(int64_t n, int64_t m, int64_t p, const int64_t* xbar, const int64_t* ybar,
+                              void* tiles, const tm_config* cfg, tm_stream_t stream) {
+    (void)cfg;
+    if (n < 0 || m < 0 || p < 1 || !aligned(xbar, 8) || !aligned(ybar, 8) || !aligned(tiles, 16))
+        return TM_ERR_INVALID;
+    return launch_plan_single(n, m, p, xbar, ybar, static_cast<TileDesc*>(tiles),
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+tm_status tm_merge_tiles(tm_key_type kt,
+                         const void* a_keys, const uint32_t* a_vals, int64_t n,
+                         const void* b_keys, const uint32_t* b_vals, int64_t m,
+                         const void* tiles, int64_t n_tiles, int32_t cap,
+                         void* c_keys, uint32_t* c_vals, void* control,
+                         const tm_config* cfg, tm_stream_t stream) {
+    if (n < 0 || m < 0 || n_tiles < 0 || cap < 1 || !aligned(control, 256)) return TM_ERR_INVALID;
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
         (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
-        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))) ||
+        (n_tiles > 0 && !aligned(tiles, 16)))
         return TM_ERR_INVALID;
-    if (n + m == 0) return TM_OK;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    switch (kt) {
-        case TM_KEY_U32: return launch_tile_merge<uint32_t>((const uint32_t*)a_keys, a_vals, n, (const uint32_t*)b_keys, b_vals, m, p, xbar, ybar, (uint32_t*)c_keys, c_vals, status, cfg, s);
-        case TM_KEY_I32: return launch_tile_merge<int32_t>((const int32_t*)a_keys, a_vals, n, (const int32_t*)b_keys, b_vals, m, p, xbar, ybar, (int32_t*)c_keys, c_vals, status, cfg, s);
-        case TM_KEY_U64: return launch_tile_merge<uint64_t>((const uint64_t*)a_keys, a_vals, n, (const uint64_t*)b_keys, b_vals, m, p, xbar, ybar, (uint64_t*)c_keys, c_vals, status, cfg, s);
-        case TM_KEY_F32: return launch_tile_merge<float>((const float*)a_keys, a_vals, n, (const float*)b_keys, b_vals, m, p, xbar, ybar, (float*)c_keys, c_vals, status, cfg, s);
-    }
-    return TM_ERR_UNSUPPORTED;
+    if (n_tiles == 0 || n + m == 0) return TM_OK;
+    return merge_tiles_dispatch(kt, a_keys, a_vals, n, b_keys, b_vals, m, tiles, n_tiles, cap,
+                                c_keys, c_vals, control, cfg, reinterpret_cast<cudaStream_t>(stream));
 }
 
 tm_status tm_subproblems(int64_t n, int64_t m, int64_t p, const int64_t* xbar,

@@ -29,11 +29,15 @@ TM_ERR_CUDA = 4
 TM_ERR_TIMEOUT = 5
 TM_ERR_BOUNDS = 6
 
+SPLIT_BLOCKS = 1
+SPLIT_DIAGONAL = 2
+
 
 class TmConfig(ctypes.Structure):
     """struct tm_config of include/tm.h (0 = default in every field)."""
     _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("grid", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
@@ -54,8 +58,12 @@ _SIGNATURES = {
     "tm_merge_workspace_size": (_SZ, [_I64, _I64, _P]),
     "tm_merge": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _SZ, _P, _P]),
     "tm_cross_ranks": (ctypes.c_int, [ctypes.c_int, _P, _I64, _P, _I64, _I64, _P, _P, _P]),
-    "tm_merge_subproblems": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _I64, _P, _P,
-                                            _P, _P, _P, _P, _P]),
+    "tm_tile_record_bytes": (_SZ, []),
+    "tm_merge_tile_cap": (_I32, [_I64, _I64, _I64]),
+    "tm_plan_tile_count": (_I64, [_I64, _I64, _I64]),
+    "tm_plan_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P, _P]),
+    "tm_merge_tiles": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P,
+                                      _P, _P]),
     "tm_rank_search": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _P, _P]),
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
@@ -182,23 +190,46 @@ def tm_cross_ranks(kt: str, A, B, p: int, xbar=None, ybar=None, stream=None):
     return xbar, ybar
 
 
-def tm_merge_subproblems(kt: str, A, Av, B, Bv, p: int, xbar, ybar, C=None, Cv=None, status=None,
-                         cfg=None, stream=None):
-    """Steps 3-4 given the cross ranks; returns (C, Cv, status)."""
+def tm_tile_record_bytes() -> int:
+    return int(load().tm_tile_record_bytes())
+
+
+def tm_merge_tile_cap(n: int, m: int, p: int) -> int:
+    return int(load().tm_merge_tile_cap(n, m, p))
+
+
+def tm_plan_tile_count(n: int, m: int, p: int) -> int:
+    return int(load().tm_plan_tile_count(n, m, p))
+
+
+def tm_plan_subproblems(n: int, m: int, p: int, xbar, ybar, tiles=None, cfg=None, stream=None):
+    """Steps 3-4 selection: tile records in merge-path order (uint8 tensor of
+    room for 2p records; the first tm_plan_tile_count(n, m, p) are valid)."""
+    if tiles is None:
+        tiles = torch.empty(2 * p * tm_tile_record_bytes(), dtype=torch.uint8, device=xbar.device)
+    code = load().tm_plan_subproblems(n, m, p, _dev(xbar, "xbar", (torch.int64,)), _dev(ybar, "ybar", (torch.int64,)),
+                                      _dev(tiles, "tiles"), _cfg(cfg), _stream(stream))
+    _check(code, "tm_plan_subproblems")
+    return tiles
+
+
+def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None, Cv=None, control=None,
+                   cfg=None, stream=None):
+    """Steps 3-4 merges of planned tiles; returns (C, Cv, control).  The
+    status word is control[0:4]."""
     kd = TORCH_KEY_DTYPES[kt]
     n, m = A.numel(), B.numel()
     if C is None:
         C = torch.empty(n + m, dtype=A.dtype, device=A.device)
     if Cv is None:
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
-    if status is None:
-        status = torch.zeros(1, dtype=torch.int32, device=A.device)
-    code = load().tm_merge_subproblems(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd),
-                                       _dev(Bv, "Bv"), m, p, _dev(xbar, "xbar", (torch.int64,)),
-                                       _dev(ybar, "ybar", (torch.int64,)), _dev(C, "C", kd), _dev(Cv, "Cv"),
-                                       _dev(status, "status", (torch.int32,)), _cfg(cfg), _stream(stream))
-    _check(code, "tm_merge_subproblems")
-    return C, Cv, status
+    if control is None:
+        control = torch.zeros(256, dtype=torch.uint8, device=A.device)
+    code = load().tm_merge_tiles(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd), _dev(Bv, "Bv"), m,
+                                 _dev(tiles, "tiles"), n_tiles, cap, _dev(C, "C", kd), _dev(Cv, "Cv"),
+                                 _dev(control, "control"), _cfg(cfg), _stream(stream))
+    _check(code, "tm_merge_tiles")
+    return C, Cv, control
 
 
 def tm_rank_search(kt: str, kind: str, q, X, out=None, stream=None):

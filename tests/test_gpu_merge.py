@@ -64,7 +64,7 @@ def test_figure1_cross_ranks_and_subproblems():
         assert a0 + b0 == c0
     Av = W.payload(0, len(g["A"]), "cpu")
     Bv = W.payload(1, len(g["B"]), "cpu")
-    gpu_merge_check("u32", A.cpu(), Av, B.cpu(), Bv, cfg={"p": p, "threads": 64})
+    gpu_merge_check("u32", A.cpu(), Av, B.cpu(), Bv, cfg={"p": p, "threads": 128})
 
 
 def test_subproblem_table_matches_five_cases_exhaustively():
@@ -90,27 +90,37 @@ def test_subproblem_table_matches_five_cases_exhaustively():
             assert got == (lo, hi, olo, ohi), (n, m, p, k, got, otable[k])
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
 @pytest.mark.parametrize("n,m", [(0, 0), (0, 7), (9, 0), (1, 1), (5, 3), (1000, 1), (4097, 4095),
                                  (30001, 20011), (100000, 3)])
-def test_small_merges_all_key_types(kt, n, m):
+def test_small_merges_all_key_types(kt, n, m, split):
     for alphabet in (None, 7):
         A, Av, B, Bv = W.small_merge(n, m, kt, seed=n * 31 + m, alphabet=alphabet)
-        gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 1024})
+        gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 1024, "split": split})
 
 
-@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+@pytest.mark.parametrize("split,threads", [(1, 128), (1, 256), (1, 512), (2, 128), (2, 256)])
 @pytest.mark.parametrize("tile", [256, 1000, 4096, 8192])
-def test_tile_and_thread_shapes(threads, tile):
+def test_tile_and_thread_shapes(threads, tile, split):
     A, Av, B, Bv = W.small_merge(70001, 50003, "u32", seed=tile + threads, alphabet=500)
-    gpu_merge_check("u32", A, Av, B, Bv, cfg={"tile": tile, "threads": threads})
+    gpu_merge_check("u32", A, Av, B, Bv, cfg={"tile": tile, "threads": threads, "split": split})
 
 
+@pytest.mark.parametrize("split,stages", [(1, 1), (1, 2), (1, 4), (2, 2), (2, 3), (2, 4)])
+@pytest.mark.parametrize("kt", ["i32", "u64"])
+def test_pipeline_depths(stages, split, kt):
+    A, Av, B, Bv = W.small_merge(200003, 150001, kt, seed=stages * 7 + split, alphabet=300)
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 2048, "stages": stages, "split": split})
+
+
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("kt", ["u32", "u64"])
 @pytest.mark.parametrize("offs", [(1, 0, 0), (0, 3, 1), (2, 1, 3), (3, 3, 2)])
-def test_unaligned_starts(kt, offs):
+def test_unaligned_starts(kt, offs, split):
     A, Av, B, Bv = W.small_merge(12345, 6789, kt, seed=sum(offs), alphabet=100)
-    gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 512}, offset_a=offs[0], offset_b=offs[1], offset_c=offs[2])
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": 512, "split": split}, offset_a=offs[0], offset_b=offs[1],
+                    offset_c=offs[2])
 
 
 def test_explicit_p_larger_than_n():
@@ -119,11 +129,12 @@ def test_explicit_p_larger_than_n():
     gpu_merge_check("u32", B, Bv, A, Av, cfg={"p": 64})
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("dist", W.DIST_NAMES)
-def test_distributions_small(dist):
+def test_distributions_small(dist, split):
     for skewed in (False, True):
         A, Av, B, Bv = W.large_merge(dist, skewed, "cpu", log2n=17, log2m_skewed=9)
-        gpu_merge_check("i32", A, Av, B, Bv)
+        gpu_merge_check("i32", A, Av, B, Bv, cfg={"split": split})
 
 
 def test_single_merge_1m_p1024():
@@ -134,6 +145,40 @@ def test_single_merge_1m_p1024():
     xo, yo = oracle.cross_ranks(to_np(A, "u32"), to_np(B, "u32"), p)
     assert np.array_equal(xbar.cpu().numpy(), xo) and np.array_equal(ybar.cpu().numpy(), yo)
     gpu_merge_check("u32", A.cpu(), Av.cpu(), B.cpu(), Bv.cpu(), cfg={"p": p})
+
+
+def test_three_phases_match_oracle_table():
+    """tm_cross_ranks -> tm_plan_subproblems -> tm_merge_tiles.  The tile
+    records (merge-path order) must be the oracle's five-case subproblems
+    of the non-empty blocks, sorted by output offset."""
+    rng = np.random.default_rng(2)
+    for n, m, p in ((5000, 3000, 7), (40000, 1, 40), (1, 9000, 5), (30000, 30000, 64), (10, 300, 64)):
+        A = np.sort(rng.integers(0, 200, n)).astype(np.uint32)
+        B = np.sort(rng.integers(0, 200, m)).astype(np.uint32)
+        dA = torch.from_numpy(A.view(np.int32)).to(DEV)
+        dB = torch.from_numpy(B.view(np.int32)).to(DEV)
+        Av = W.payload(0, n, DEV)
+        Bv = W.payload(1, m, DEV)
+        xbar, ybar = tm.tm_cross_ranks("u32", dA, dB, p)
+        tiles = tm.tm_plan_subproblems(n, m, p, xbar, ybar)
+        count = tm.tm_plan_tile_count(n, m, p)
+        rec = tiles.view(torch.int64).view(2 * p, 4)[:count].cpu().numpy()
+        otable = oracle.subproblems(n, m, p, xbar.cpu().numpy(), ybar.cpu().numpy())
+        expect = []
+        for k in range(2 * p):
+            lo, hi, olo, ohi, oc0, case = otable[k]
+            if hi == lo and ohi == olo:
+                continue
+            a = (lo, hi, olo, ohi) if k < p else (olo, ohi, lo, hi)
+            expect.append((oc0, a[0], a[1] - a[0], a[2], a[3] - a[2]))
+        expect.sort()
+        got = [(int(r[2]), int(r[0]), int(r[3] & 0xffffffff), int(r[1]), int(r[3] >> 32)) for r in rec]
+        assert got == expect, (n, m, p)
+        cap = tm.tm_merge_tile_cap(n, m, p)
+        C, Cv, control = tm.tm_merge_tiles("u32", dA, Av, dB, Bv, tiles, count, cap)
+        assert tm.tm_read_status(control) == 0
+        K, V = oracle.merge_two_pointer(A, vals_np(Av), B, vals_np(Bv))
+        assert np.array_equal(to_np(C, "u32"), K) and np.array_equal(vals_np(Cv), V)
 
 
 def test_rank_search_against_oracle():
