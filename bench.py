@@ -220,6 +220,100 @@ def cpu_baseline(items):
                       "two-pointer merge of oracle/tm_oracle.c", "seconds": dt}
 
 
+def bench_batched(dev, steps: int = 10):
+    """Batched form: 65,536 independent pairs (lengths log-uniform in
+    [1, 2**16] per side, u64 keys + u32 payloads), autotuned, captured in a
+    CUDA graph, replayed `steps` times.  Compared with the plain form: the
+    same pairs as 65,536 tm_merge calls on one stream."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    a_off, A, Av, b_off, B, Bv = W.batched_pairs(dev)
+    pairs = a_off.numel() - 1
+    ta, tb = A.numel(), B.numel()
+    total = ta + tb
+    C = torch.empty(total, dtype=torch.int64, device=dev)
+    Cv = torch.empty(total, dtype=torch.int32, device=dev)
+    big = max(tm.tm_merge_batched_workspace_size(pairs, ta, tb, {"tile": t}) for t in (1024, 2048, 4096))
+    ws = tm.new_workspace(big, dev)
+    s = torch.cuda.Stream(dev)
+    best = tm.tm_autotune_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, stream=s)
+    tm.tm_merge_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, cfg=best, stream=s)
+    s.synchronize()
+    with tm.Graph(s) as g:
+        tm.tm_merge_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, cfg=best, stream=s)
+    for _ in range(2):
+        g.launch()
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        g.launch()
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert tm.tm_read_status(ws, stream=s) == 0
+    # plain form: one tm_merge per pair (host loop, one stream)
+    ho_a, ho_b = a_off.cpu().tolist(), b_off.cpu().tolist()
+    wsp = tm.new_workspace(tm.tm_merge_workspace_size(1 << 16, 1 << 16), dev)
+    def plain():
+        for k in range(pairs):
+            a0, a1, b0, b1 = ho_a[k], ho_a[k + 1], ho_b[k], ho_b[k + 1]
+            c0 = a0 + b0
+            L = (a1 - a0) + (b1 - b0)
+            tm.tm_merge("u64", A[a0:a1], Av[a0:a1], B[b0:b1], Bv[b0:b1], C[c0:c0 + L], Cv[c0:c0 + L], wsp, stream=s)
+    plain()
+    s.synchronize()
+    e0.record(s)
+    plain()
+    e1.record(s)
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    gbs = total * 24 / (ms / 1e3) / 1e9
+    return {"workload": "65,536 pairs, lengths log-uniform in [1, 2^16] per side, u64 keys in [0, 2^20) + u32 "
+                        "payloads; autotuned; one CUDA graph (count, scan, search, plan, persistent merge)",
+            "elements": total, "value": total / (ms / 1e3), "unit": UNIT, "ms": ms, "steps": steps,
+            "config": best, "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0],
+            "plain_per_pair_tm_merge": {"value": total / (ms_plain / 1e3), "ms": ms_plain,
+                                        "calls": pairs},
+            "speedup_vs_plain": ms_plain / ms}
+
+
+def bench_sort(dev, steps: int = 3):
+    """Stable merge sort of 2**28 u64 keys uniform in [0, 2**24) with u32
+    payloads (original index): sorted runs of 1024, then 18 merge rounds."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    src_k, src_v = W.sort_input(dev)
+    n = src_k.numel()
+    keys, vals = torch.empty_like(src_k), torch.empty_like(src_v)
+    tk, tv = torch.empty_like(src_k), torch.empty_like(src_v)
+    big = max(tm.tm_merge_sort_workspace_size(n, {"tile": t}) for t in (1024, 2048, 4096))
+    ws = tm.new_workspace(big, dev)
+    s = torch.cuda.Stream(dev)
+    best = tm.tm_autotune_sort("u64", src_k, src_v, keys, vals, tk, tv, ws, stream=s)
+    times = []
+    for _ in range(steps + 1):
+        keys.copy_(src_k)
+        vals.copy_(src_v)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        tm.tm_merge_sort("u64", keys, vals, tk, tv, ws, cfg=best, stream=s)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert tm.tm_read_status(ws, stream=s) == 0
+    ms = float(np.median(times[1:]))
+    rounds = 0
+    r = 1024
+    while r < n:
+        r *= 2
+        rounds += 1
+    moved = n * 24 * (rounds + 1)               # run formation + every merge round read and write 12 B
+    return {"workload": "stable merge sort of 2^28 u64 keys uniform in [0, 2^24) + u32 payloads",
+            "elements": n, "value": n / (ms / 1e3), "unit": "sorted elems/s", "ms": ms, "rounds": rounds,
+            "config": best, "passes_gbs": moved / (ms / 1e3) / 1e9,
+            "frac_of_hbm": moved / (ms / 1e3) / 1e9 / measured_peaks()[0]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +330,7 @@ def main():
     ap.add_argument("--dists", default="", help="comma list of distributions (default: all four)")
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and merge-sort forms")
     args = ap.parse_args()
     args.dists = [d for d in args.dists.split(",") if d] or None
     rank, local_rank, world = env_rank()
@@ -398,20 +493,28 @@ def main():
             cpu = cpu_baseline(items)
 
     clocks = sampler.summary(power_floor_w=200.0)
+    forms = None
+    n_merges, p_first = len(items), items[0]["p"]
+    if not args.no_forms:
+        for it in items:
+            it.clear()
+        torch.cuda.empty_cache()
+        forms = {"batched": bench_batched(dev), "merge_sort": bench_sort(dev)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "elements_per_step": elems_per_step,
-                           "merges_per_step": len(items), "tile": args.tile or 2048,
-                           "blocks_p": items[0]["p"],
+                           "merges_per_step": n_merges, "tile": args.tile or 2048,
+                           "blocks_p": p_first,
                            "threads": args.threads or 128, "stages": args.stages or "auto",
                            "split": {0: "diagonal (default)", 1: "blocks", 2: "diagonal"}[args.split], "l2": "inputs larger than L2 (2-4 GB per merge)",
                            "parallelism": f"replicas x{world}"},
                 "per_merge_ms": per_item_merge_ms,
+                "forms": forms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * len(items) * args.steps}
+                "gpu_launches": 3 * n_merges * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

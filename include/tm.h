@@ -159,8 +159,9 @@ TM_API tm_status tm_cross_ranks(tm_key_type kt,
  * the subproblem's A range, B range and output offset, chosen by the five
  * cases (a)-(e) of Step 3 and their mirror in Step 4.  Records are stored
  * in merge-path order (by output offset), tm_plan_tile_count(n, m, p) of
- * them; `tiles` must hold 2p records.  Layout of a record: int64 a0, b0, c0
- * (first A index, first B index, first output index), int32 nA, nB. */
+ * them; `tiles` must hold 2p records.  Layout of a record (48 bytes):
+ * int64 a0, b0, c0 (first A index, first B index, first output index),
+ * int32 nA, nB, int32 first (1 on a merge's first record), padding. */
 TM_API size_t tm_tile_record_bytes(void);
 TM_API int64_t tm_plan_tile_count(int64_t n, int64_t m, int64_t p);
 TM_API tm_status tm_plan_subproblems(int64_t n, int64_t m, int64_t p,
@@ -194,6 +195,84 @@ TM_API tm_status tm_merge_tiles(tm_key_type kt,
 TM_API tm_status tm_subproblems(int64_t n, int64_t m, int64_t p,
                                 const int64_t* xbar, const int64_t* ybar,
                                 int64_t* table, tm_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Many merges at once and the stable merge sort (Section 3)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes of tm_merge_batched for (num_pairs, total_a, total_b, cfg). */
+TM_API size_t tm_merge_batched_workspace_size(int64_t num_pairs, int64_t total_a, int64_t total_b,
+                                              const tm_config* cfg);
+
+/* num_pairs independent stable merges.  Pair k merges A[a_offsets[k] ..
+ * a_offsets[k+1]) with B[b_offsets[k] .. b_offsets[k+1]) into C from
+ * a_offsets[k] + b_offsets[k] (CSR offsets, device int64, num_pairs + 1
+ * each, starting at 0 and ending at total_a / total_b).  Each pair is merged
+ * by the paper's method with its own block count p_k = ceil((n_k + m_k) /
+ * tile): one search kernel and one planning kernel cover all pairs, then one
+ * persistent tile-merge launch pulls every pair's subproblems from a device
+ * work queue.  No host synchronisation: the call can be captured in a CUDA
+ * graph (tm_graph_capture_begin/end).  cfg NULL uses the configuration the
+ * autotuner chose for this key type and size, if any, else the defaults.
+ * The status word is the first 4 bytes of the workspace. */
+TM_API tm_status tm_merge_batched(tm_key_type kt, int64_t num_pairs,
+                                  const int64_t* a_offsets, const void* a_keys, const uint32_t* a_vals,
+                                  int64_t total_a,
+                                  const int64_t* b_offsets, const void* b_keys, const uint32_t* b_vals,
+                                  int64_t total_b,
+                                  void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
+                                  const tm_config* cfg, tm_stream_t stream);
+
+/* Workspace bytes of tm_merge_sort for n elements. */
+TM_API size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg);
+
+/* Stable sort of (keys, vals) by key (Section 3): consecutive runs of 1024
+ * elements are sorted inside one CTA each (every element placed by the
+ * position formulas of Section 2 over doubling sub-runs), then ceil(log2(n /
+ * 1024)) rounds merge adjacent runs pairwise, every round one batched merge
+ * of uniform pairs (an unpaired last run is copied).  Rounds alternate
+ * between (keys, vals) and (tmp_keys, tmp_vals); the result ends in (keys,
+ * vals).  Equal keys keep their input order. */
+TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n,
+                               void* tmp_keys, uint32_t* tmp_vals, void* workspace, size_t workspace_bytes,
+                               const tm_config* cfg, tm_stream_t stream);
+
+/* Autotuner (not in the paper): runs tm_merge_batched (resp. tm_merge_sort on
+ * a fresh device copy of src into keys/vals per trial) once per candidate
+ * configuration -- tile {1024, 2048, 4096} x threads {128, 256} x stages
+ * {3, 4}, diagonal in-CTA split, skipping those whose workspace exceeds
+ * workspace_bytes -- timed with CUDA events on `stream`, and keeps the
+ * fastest for later calls with cfg NULL on the same key type and size
+ * (power-of-two bucket of the element count).  Synchronises the stream.
+ * *best receives the chosen configuration. */
+TM_API tm_status tm_autotune_batched(tm_key_type kt, int64_t num_pairs,
+                                     const int64_t* a_offsets, const void* a_keys, const uint32_t* a_vals,
+                                     int64_t total_a,
+                                     const int64_t* b_offsets, const void* b_keys, const uint32_t* b_vals,
+                                     int64_t total_b,
+                                     void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
+                                     tm_config* best, tm_stream_t stream);
+TM_API tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t* src_vals, int64_t n,
+                                  void* keys, uint32_t* vals, void* tmp_keys, uint32_t* tmp_vals,
+                                  void* workspace, size_t workspace_bytes, tm_config* best,
+                                  tm_stream_t stream);
+/* Forgets every autotuned configuration; returns how many there were. */
+TM_API int tm_autotune_clear(void);
+
+/* ------------------------------------------------------------------------ */
+/* CUDA graphs                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Capture every call issued on `stream` (not the legacy NULL stream) between
+ * begin and end into a CUDA graph (thread-local capture mode); replay it
+ * with tm_graph_launch on any stream.  The replay reuses the pointers and
+ * sizes of the captured calls.  tm_graph_end returns TM_ERR_CUDA if the
+ * capture failed (e.g. a call synchronised the stream). */
+typedef struct tm_graph tm_graph;
+TM_API tm_status tm_graph_capture_begin(tm_stream_t stream);
+TM_API tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out);
+TM_API tm_status tm_graph_launch(tm_graph* g, tm_stream_t stream);
+TM_API void tm_graph_destroy(tm_graph* g);
 
 /* Stable merge that allocates nothing and needs no workspace.  The paper has
  * no counterpart; this is a convenience of the library.  It exists for

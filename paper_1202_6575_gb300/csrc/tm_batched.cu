@@ -1,0 +1,677 @@
+// Many independent stable merges at once (Section 3: the merge applied in
+// parallel to several pairs) and the stable merge sort built from it.
+//
+// Each pair k gets its own block count p_k and runs the single-merge method:
+// cross-rank searches of its block starts (one search kernel over all pairs),
+// subproblem selection (one plan kernel over all pairs, records in
+// merge-path order per pair), then one launch of the persistent tile engine
+// over every pair's records, which pulls them from its device work queue.
+// Every grid is sized from host-known bounds and the engine reads the record
+// count from device memory, so a whole batched merge is one stream sequence
+// with no host synchronisation and can be captured in a CUDA graph.
+#include <cstring>
+#include <new>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "tm_engine.cuh"
+#include "tm_host.h"
+
+namespace pmerge {
+
+// A set of pairs: either CSR offsets (pair k merges A[a_off[k]..a_off[k+1])
+// with B[b_off[k]..b_off[k+1]) into C from a_off[k] + b_off[k]), or uniform
+// runs of one array (pair k merges the sorted runs [2k*run, (2k+1)*run) and
+// [(2k+1)*run, (2k+2)*run) of X, clipped to `total`, into C from 2k*run).
+struct PairSet {
+    int64_t num_pairs;
+    const int64_t* a_off;
+    const int64_t* b_off;
+    int64_t run, total;            // uniform mode when a_off == nullptr
+    int64_t p_uniform;             // blocks per pair in uniform mode
+
+    __device__ __forceinline__ void get(int64_t k, int64_t& a0, int64_t& n, int64_t& b0, int64_t& m,
+                                        int64_t& c0) const {
+        if (a_off) {
+            a0 = a_off[k]; n = a_off[k + 1] - a0;
+            b0 = b_off[k]; m = b_off[k + 1] - b0;
+            c0 = a0 + b0;
+        } else {
+            a0 = 2 * k * run;
+            n = total - a0 < run ? total - a0 : run;
+            b0 = a0 + n;
+            m = total - b0 < run ? total - b0 : run;
+            if (m < 0) m = 0;
+            c0 = a0;
+        }
+    }
+};
+
+// Per-pair block count: enough blocks that one subproblem fits `tile`.
+__host__ __device__ __forceinline__ int64_t pair_blocks(int64_t n, int64_t m, int64_t tile) {
+    const int64_t len = n + m;
+    if (len == 0) return 0;
+    const int64_t p = (len + tile - 1) / tile;
+    return p < 1 ? 1 : p;
+}
+
+__host__ __device__ __forceinline__ int64_t pair_items(int64_t n, int64_t m, int64_t p) {
+    return (n < p ? n : p) + (m < p ? m : p);
+}
+
+// Bases of pair k (uniform mode: closed form; CSR mode: scanned arrays).
+struct PairBases {
+    const int64_t* search_base;    // 2 p_k prefix      (CSR)
+    const int64_t* rank_base;      // (p_k + 1) prefix  (CSR)
+    const int64_t* item_base;      // items prefix      (CSR)
+};
+
+// ---------------------------------------------------------------------------
+// CSR mode: per-pair counts and their exclusive scans
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+pair_count_kernel(PairSet ps, int64_t tile, int64_t* __restrict__ cnt_search, int64_t* __restrict__ cnt_rank,
+                  int64_t* __restrict__ cnt_item) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ps.num_pairs) return;
+    int64_t a0, n, b0, m, c0;
+    ps.get(k, a0, n, b0, m, c0);
+    const int64_t p = pair_blocks(n, m, tile);
+    cnt_search[k] = 2 * p;
+    cnt_rank[k] = p + 1;
+    cnt_item[k] = pair_items(n, m, p);
+}
+
+// Exclusive scans of three count arrays in place (one CTA of 1024 threads,
+// each scanning a contiguous chunk).  base[num] receives the totals; the
+// record total also goes to *n_items.
+__global__ void __launch_bounds__(1024)
+scan3_kernel(int64_t num, int64_t* __restrict__ s0, int64_t* __restrict__ s1, int64_t* __restrict__ s2,
+             int64_t* __restrict__ n_items) {
+    __shared__ int64_t part[3][1024];
+    const int t = threadIdx.x;
+    const int64_t chunk = (num + 1023) / 1024;
+    const int64_t lo = t * chunk < num ? t * chunk : num;
+    const int64_t hi = lo + chunk < num ? lo + chunk : num;
+    int64_t a = 0, b = 0, c = 0;
+    for (int64_t i = lo; i < hi; ++i) { a += s0[i]; b += s1[i]; c += s2[i]; }
+    part[0][t] = a; part[1][t] = b; part[2][t] = c;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {       // inclusive Hillis-Steele scan of the partials
+        int64_t x0 = 0, x1 = 0, x2 = 0;
+        if (t >= off) { x0 = part[0][t - off]; x1 = part[1][t - off]; x2 = part[2][t - off]; }
+        __syncthreads();
+        part[0][t] += x0; part[1][t] += x1; part[2][t] += x2;
+        __syncthreads();
+    }
+    int64_t r0 = t ? part[0][t - 1] : 0, r1 = t ? part[1][t - 1] : 0, r2 = t ? part[2][t - 1] : 0;
+    for (int64_t i = lo; i < hi; ++i) {
+        const int64_t v0 = s0[i], v1 = s1[i], v2 = s2[i];
+        s0[i] = r0; s1[i] = r1; s2[i] = r2;
+        r0 += v0; r1 += v1; r2 += v2;
+    }
+    if (t == 1023) {
+        s0[num] = part[0][1023]; s1[num] = part[1][1023]; s2[num] = part[2][1023];
+        *n_items = part[2][1023];
+    }
+}
+
+// Pair owning global search index t: the last k with search_base[k] <= t.
+__device__ __forceinline__ int64_t pair_of(const int64_t* base, int64_t num, int64_t t) {
+    int64_t lo = 0, len = num;                        // first k with base[k] > t, minus one
+    while (len > 0) {
+        const int64_t half = len >> 1;
+        if (__ldg(base + lo + half + 1) <= t) { lo += half + 1; len -= half + 1; } else { len = half; }
+    }
+    return lo;
+}
+
+// Maps a global (search or plan) thread index to (pair, local index).
+__device__ __forceinline__ bool locate(const PairSet& ps, const PairBases& pb, int64_t t, int64_t& k,
+                                       int64_t& local, int64_t& p) {
+    if (ps.a_off) {
+        if (t >= __ldg(pb.search_base + ps.num_pairs)) return false;
+        k = pair_of(pb.search_base, ps.num_pairs, t);
+        local = t - __ldg(pb.search_base + k);
+        p = (__ldg(pb.search_base + k + 1) - __ldg(pb.search_base + k)) / 2;
+    } else {
+        p = ps.p_uniform;
+        k = t / (2 * p);
+        if (k >= ps.num_pairs) return false;
+        local = t - k * 2 * p;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int64_t rank_base_of(const PairSet& ps, const PairBases& pb, int64_t k) {
+    return ps.a_off ? __ldg(pb.rank_base + k) : k * (ps.p_uniform + 1);
+}
+
+__device__ __forceinline__ int64_t item_base_of(const PairSet& ps, const PairBases& pb, int64_t k) {
+    return ps.a_off ? __ldg(pb.item_base + k) : k * 2 * ps.p_uniform;
+}
+
+// Steps 1-2 of every pair.
+template <typename K>
+__global__ void __launch_bounds__(256)
+batched_search_kernel(PairSet ps, PairBases pb, const K* __restrict__ A, const K* __restrict__ B,
+                      int64_t total_threads, int64_t* __restrict__ xbar, int64_t* __restrict__ ybar) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_threads) return;
+    int64_t k, local, p;
+    if (!locate(ps, pb, t, k, local, p)) return;
+    int64_t a0, n, b0, m, c0;
+    ps.get(k, a0, n, b0, m, c0);
+    const int64_t rb = rank_base_of(ps, pb, k);
+    if (local < p) {
+        const int64_t xi = block_start<int64_t>(n, p, local);
+        xbar[rb + local] = (xi < n) ? rank_low_global<K, int64_t>(B + b0, m, __ldg(A + a0 + xi)) : m;
+        if (local == 0) { xbar[rb + p] = m; ybar[rb + p] = n; }
+    } else {
+        const int64_t j = local - p;
+        const int64_t yj = block_start<int64_t>(m, p, j);
+        ybar[rb + j] = (yj < m) ? rank_high_global<K, int64_t>(A + a0, n, __ldg(B + b0 + yj)) : n;
+    }
+}
+
+// Steps 3-4 selection of every pair: records in merge-path order per pair,
+// at global offsets, the pair's first record flagged.
+__global__ void __launch_bounds__(256)
+batched_plan_kernel(PairSet ps, PairBases pb, int64_t total_threads, const int64_t* __restrict__ xbar,
+                    const int64_t* __restrict__ ybar, TileDesc* __restrict__ desc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_threads) return;
+    int64_t k, local, p;
+    if (!locate(ps, pb, t, k, local, p)) return;
+    int64_t a0g, n, b0g, m, c0g;
+    ps.get(k, a0g, n, b0g, m, c0g);
+    const bool a_side = local < p;
+    const int64_t pe = a_side ? local : local - p;
+    if (a_side ? block_start<int64_t>(n, p, pe) >= n : block_start<int64_t>(m, p, pe) >= m) return;
+    const int64_t rb = rank_base_of(ps, pb, k);
+    auto xb = [&](int64_t i) { return __ldg(xbar + rb + i); };
+    auto yb = [&](int64_t j) { return __ldg(ybar + rb + j); };
+    int64_t a0, a1, b0, b1;
+    subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
+    const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
+                                 : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
+    TileDesc d{};
+    d.a0 = a0g + a0; d.b0 = b0g + b0; d.c0 = c0g + a0 + b0;
+    d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);
+    d.first = chain == 0;
+    desc[item_base_of(ps, pb, k) + chain] = d;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <typename K>
+tm_status launch_engine(const EngineArgs& a, const tm_config* cfg, cudaStream_t s);
+
+struct BatchedWs {
+    void* control;
+    int64_t* n_items;                              // device record count
+    int64_t *search_base, *rank_base, *item_base;  // num_pairs + 1 each (CSR)
+    int64_t *xbar, *ybar;
+    TileDesc* tiles;
+    size_t bytes;
+};
+
+static int64_t tile_of(const tm_config* cfg) { return (cfg && cfg->tile > 0) ? cfg->tile : kDefaultTile; }
+
+// Bounds: p_k <= (n_k + m_k) / tile + 1, so sum p_k <= total / tile + pairs.
+static int64_t blocks_bound(int64_t pairs, int64_t total, int64_t tile) { return total / tile + pairs; }
+
+// Workspace: control block, device record count, three per-pair prefix
+// arrays, cross ranks (ranks_cap entries per side) and tile records.
+static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap) {
+    BatchedWs w{};
+    uint8_t* b = static_cast<uint8_t*>(base);
+    size_t o = 0;
+    w.control = b; o += kStatusBytes;
+    w.n_items = reinterpret_cast<int64_t*>(b + o); o += 256;
+    w.search_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
+    w.rank_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
+    w.item_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
+    w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
+    w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
+    w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)items_cap * sizeof(TileDesc), 256);
+    w.bytes = o;
+    return w;
+}
+
+// CSR pairs: sum (p_k + 1) <= P + pairs and sum items <= 2 P.
+static BatchedWs batched_ws_layout(void* base, int64_t pairs, int64_t total, int64_t tile) {
+    const int64_t P = blocks_bound(pairs, total, tile);
+    return ws_layout(base, pairs, P + pairs, 2 * P);
+}
+
+// Runs search, plan and the engine for a pair set; `ws` laid out as above.
+template <typename K>
+static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_a, int64_t total_b,
+                           const K* A, const uint32_t* Av, const K* B, const uint32_t* Bv,
+                           K* C, uint32_t* Cv, int64_t tile, int64_t known_items,
+                           const tm_config* cfg, cudaStream_t s) {
+    const int64_t total = total_a + total_b;
+    PairBases pb{w.search_base, w.rank_base, w.item_base};
+    int64_t threads;                               // upper bound of sum 2 p_k
+    if (ps.a_off) {
+        const int64_t blocks = (ps.num_pairs + 255) / 256;
+        pair_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps, tile, w.search_base, w.rank_base, w.item_base);
+        scan3_kernel<<<1, 1024, 0, s>>>(ps.num_pairs, w.search_base, w.rank_base, w.item_base, w.n_items);
+        threads = 2 * blocks_bound(ps.num_pairs, total, tile);
+    } else {
+        threads = 2 * ps.p_uniform * ps.num_pairs;
+    }
+    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    const int64_t grid = (threads + 255) / 256;
+    if (grid > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    if (grid > 0) {
+        batched_search_kernel<K><<<(unsigned)grid, 256, 0, s>>>(ps, pb, A, B, threads, w.xbar, w.ybar);
+        batched_plan_kernel<<<(unsigned)grid, 256, 0, s>>>(ps, pb, threads, w.xbar, w.ybar, w.tiles);
+    }
+    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    EngineArgs a{};
+    a.desc = w.tiles;
+    a.n_items = known_items;                       // -1 in CSR mode: read from the device
+    a.n_items_dev = w.n_items;
+    a.items_bound = known_items >= 0 ? known_items : 2 * blocks_bound(ps.num_pairs, total, tile);
+    a.status = static_cast<int32_t*>(w.control);
+    a.queue = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(w.control) + 8);
+    a.A = A; a.Av = Av; a.lenA = total_a;
+    a.B = B; a.Bv = Bv; a.lenB = total_b;
+    a.C = C; a.Cv = Cv;
+    a.cap = (int)(tile + 2);
+    if (a.items_bound == 0) return TM_OK;
+    return launch_engine<K>(a, cfg, s);
+}
+
+template <typename K>
+static tm_status batched_typed(int64_t pairs, const int64_t* a_off, const void* a_keys, const uint32_t* a_vals,
+                               int64_t total_a, const int64_t* b_off, const void* b_keys, const uint32_t* b_vals,
+                               int64_t total_b, void* c_keys, uint32_t* c_vals, void* ws,
+                               const tm_config* cfg, cudaStream_t s) {
+    const int64_t tile = tile_of(cfg);
+    BatchedWs w = batched_ws_layout(ws, pairs, total_a + total_b, tile);
+    if (cudaMemsetAsync(w.control, 0, 16, s) != cudaSuccess) return TM_ERR_CUDA;
+    if (pairs == 0 || total_a + total_b == 0) return TM_OK;
+    PairSet ps{};
+    ps.num_pairs = pairs; ps.a_off = a_off; ps.b_off = b_off;
+    return run_pairs<K>(ps, w, total_a, total_b, static_cast<const K*>(a_keys), a_vals,
+                        static_cast<const K*>(b_keys), b_vals, static_cast<K*>(c_keys), c_vals,
+                        tile, -1, cfg, s);
+}
+
+// ---------------------------------------------------------------------------
+// Stable merge sort (Section 3): stable sorted runs, then merge rounds
+// ---------------------------------------------------------------------------
+
+// Stable in-CTA sort of consecutive runs of RUN elements: every element's
+// final place within its run is found with the position formulas of
+// Section 2 applied to pairs of sorted sub-runs (A-side elements at
+// i + rank_low, B-side at j + rank_high), doubling the sub-run length from 1
+// to RUN; sub-runs ping-pong between two shared-memory buffers.
+template <typename K, int RUN>
+__global__ void __launch_bounds__(RUN)
+run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K* __restrict__ out_k,
+                uint32_t* __restrict__ out_v, int64_t n) {
+    __shared__ K sk[2][RUN];
+    __shared__ uint32_t sv[2][RUN];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * RUN;
+    const int len = (int)(n - base < RUN ? n - base : RUN);
+    if (t < len) { sk[0][t] = in_k[base + t]; sv[0][t] = in_v[base + t]; }
+    __syncthreads();
+    int cur = 0;
+    for (int w = 1; w < len; w <<= 1) {
+        if (t < len) {
+            const int lo = t & ~(2 * w - 1);               // pair start
+            const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
+            const K key = sk[cur][t];
+            int pos;
+            if (t < mid) {                                   // A side: i + rank_low(A[i], B)
+                const K* Bp = &sk[cur][mid];
+                int r = 0, l = hi - mid;
+                while (l > 0) { int h = l >> 1; if (Bp[r + h] < key) { r += h + 1; l -= h + 1; } else l = h; }
+                pos = lo + (t - lo) + r;
+            } else {                                         // B side: j + rank_high(B[j], A)
+                const K* Ap = &sk[cur][lo];
+                int r = 0, l = mid - lo;
+                while (l > 0) { int h = l >> 1; if (!(key < Ap[r + h])) { r += h + 1; l -= h + 1; } else l = h; }
+                pos = lo + (t - mid) + r;
+            }
+            sk[cur ^ 1][pos] = key;
+            sv[cur ^ 1][pos] = sv[cur][t];
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (t < len) { out_k[base + t] = sk[cur][t]; out_v[base + t] = sv[cur][t]; }
+}
+
+constexpr int kSortRun = 1024;
+
+// Pair set of the merge round with sorted runs of length `run`.
+static PairSet sort_round(int64_t n, int64_t run, int64_t tile, int64_t* items) {
+    PairSet ps{};
+    ps.num_pairs = (n + 2 * run - 1) / (2 * run);
+    ps.run = run; ps.total = n;
+    ps.p_uniform = pair_blocks(run, run, tile);
+    const int64_t last_a0 = 2 * (ps.num_pairs - 1) * run;
+    const int64_t last_n = n - last_a0 < run ? n - last_a0 : run;
+    int64_t last_m = n - last_a0 - last_n < run ? n - last_a0 - last_n : run;
+    if (last_m < 0) last_m = 0;
+    *items = (ps.num_pairs - 1) * 2 * ps.p_uniform + pair_items(last_n, last_m, ps.p_uniform);
+    return ps;
+}
+
+// The largest rank and record counts over all merge rounds.
+static BatchedWs sort_ws_layout(void* base, int64_t n, int64_t tile) {
+    int64_t ranks = 0, items = 0;
+    for (int64_t run = kSortRun; run < n; run *= 2) {
+        int64_t it = 0;
+        PairSet ps = sort_round(n, run, tile, &it);
+        const int64_t r = ps.num_pairs * (ps.p_uniform + 1);
+        if (r > ranks) ranks = r;
+        if (2 * ps.num_pairs * ps.p_uniform > items) items = 2 * ps.num_pairs * ps.p_uniform;
+    }
+    return ws_layout(base, 0, ranks, items);
+}
+
+template <typename K>
+static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
+                            void* ws, const tm_config* cfg, cudaStream_t s) {
+    const int64_t tile = tile_of(cfg);
+    BatchedWs w = sort_ws_layout(ws, n, tile);
+    if (cudaMemsetAsync(w.control, 0, 16, s) != cudaSuccess) return TM_ERR_CUDA;
+    if (n <= 1) return TM_OK;
+    K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
+    uint32_t* bufv[2] = {vals, tmp_vals};
+    // number of merge rounds decides where the run formation writes, so that
+    // the last round lands in (keys, vals)
+    int rounds = 0;
+    for (int64_t r = kSortRun; r < n; r *= 2) ++rounds;
+    int src = (rounds % 2 == 0) ? 0 : 1;
+    const int64_t runs = (n + kSortRun - 1) / kSortRun;
+    if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    run_sort_kernel<K, kSortRun><<<(unsigned)runs, kSortRun, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
+    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    for (int64_t run = kSortRun; run < n; run *= 2) {
+        int64_t items = 0;
+        const PairSet ps = sort_round(n, run, tile, &items);
+        const int dst = src ^ 1;
+        tm_status st = run_pairs<K>(ps, w, n, n, bufk[src], bufv[src], bufk[src], bufv[src],
+                                    bufk[dst], bufv[dst], tile, items, cfg, s);
+        if (st != TM_OK) return st;
+        src = dst;
+    }
+    return TM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times candidate configurations on the caller's data with CUDA
+// events and remembers the fastest per (key type, size bucket, operation).
+// ---------------------------------------------------------------------------
+
+struct TuneKey {
+    int op, kt, log2_total;
+    bool operator<(const TuneKey& o) const { return std::tie(op, kt, log2_total) < std::tie(o.op, o.kt, o.log2_total); }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, tm_config> g_tune;
+
+static int log2_bucket(int64_t x) { int b = 0; while ((int64_t(1) << (b + 1)) <= x) ++b; return b; }
+
+static bool tuned_config(int op, tm_key_type kt, int64_t total, tm_config* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(TuneKey{op, (int)kt, log2_bucket(total)});
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+}  // namespace pmerge
+
+using namespace pmerge;
+
+namespace {
+tm_status check_batched(tm_key_type kt, int64_t pairs, const int64_t* a_off, const void* a_keys,
+                        const uint32_t* a_vals, int64_t total_a, const int64_t* b_off, const void* b_keys,
+                        const uint32_t* b_vals, int64_t total_b, void* c_keys, uint32_t* c_vals) {
+    if (pairs < 0 || total_a < 0 || total_b < 0) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if (pairs > 0 && (!aligned(a_off, 8) || !aligned(b_off, 8))) return TM_ERR_INVALID;
+    if ((total_a > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
+        (total_b > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
+        (total_a + total_b > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+        return TM_ERR_INVALID;
+    return TM_OK;
+}
+
+tm_status batched_dispatch(tm_key_type kt, int64_t pairs, const int64_t* a_off, const void* a_keys,
+                           const uint32_t* a_vals, int64_t total_a, const int64_t* b_off, const void* b_keys,
+                           const uint32_t* b_vals, int64_t total_b, void* c_keys, uint32_t* c_vals,
+                           void* ws, const tm_config* cfg, cudaStream_t s) {
+    switch (kt) {
+        case TM_KEY_U32: return batched_typed<uint32_t>(pairs, a_off, a_keys, a_vals, total_a, b_off, b_keys, b_vals, total_b, c_keys, c_vals, ws, cfg, s);
+        case TM_KEY_I32: return batched_typed<int32_t>(pairs, a_off, a_keys, a_vals, total_a, b_off, b_keys, b_vals, total_b, c_keys, c_vals, ws, cfg, s);
+        case TM_KEY_U64: return batched_typed<uint64_t>(pairs, a_off, a_keys, a_vals, total_a, b_off, b_keys, b_vals, total_b, c_keys, c_vals, ws, cfg, s);
+        case TM_KEY_F32: return batched_typed<float>(pairs, a_off, a_keys, a_vals, total_a, b_off, b_keys, b_vals, total_b, c_keys, c_vals, ws, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+}  // namespace
+
+extern "C" {
+
+size_t tm_merge_batched_workspace_size(int64_t num_pairs, int64_t total_a, int64_t total_b, const tm_config* cfg) {
+    if (num_pairs < 0 || total_a < 0 || total_b < 0) return 0;
+    return batched_ws_layout(nullptr, num_pairs, total_a + total_b, tile_of(cfg)).bytes;
+}
+
+tm_status tm_merge_batched(tm_key_type kt, int64_t num_pairs,
+                           const int64_t* a_offsets, const void* a_keys, const uint32_t* a_vals, int64_t total_a,
+                           const int64_t* b_offsets, const void* b_keys, const uint32_t* b_vals, int64_t total_b,
+                           void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
+                           const tm_config* cfg, tm_stream_t stream) {
+    tm_status st = check_batched(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
+                                 total_b, c_keys, c_vals);
+    if (st != TM_OK) return st;
+    tm_config tuned;
+    if (!cfg && tuned_config(1, kt, total_a + total_b, &tuned)) cfg = &tuned;
+    if (!workspace || !aligned(workspace, 256) ||
+        workspace_bytes < tm_merge_batched_workspace_size(num_pairs, total_a, total_b, cfg))
+        return TM_ERR_WORKSPACE;
+    return batched_dispatch(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
+                            total_b, c_keys, c_vals, workspace, cfg, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg) {
+    if (n < 0) return 0;
+    return sort_ws_layout(nullptr, n, tile_of(cfg)).bytes;
+}
+
+tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
+                        void* workspace, size_t workspace_bytes, const tm_config* cfg, tm_stream_t stream) {
+    if (n < 0) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if (n > 0 && (!aligned(keys, E) || !aligned(vals, 4) || !aligned(tmp_keys, E) || !aligned(tmp_vals, 4)))
+        return TM_ERR_INVALID;
+    tm_config tuned;
+    if (!cfg && tuned_config(2, kt, n, &tuned)) cfg = &tuned;
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < tm_merge_sort_workspace_size(n, cfg))
+        return TM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return sort_typed<uint32_t>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
+        case TM_KEY_I32: return sort_typed<int32_t>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
+        case TM_KEY_U64: return sort_typed<uint64_t>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
+        case TM_KEY_F32: return sort_typed<float>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Candidate configurations: tile x consumer threads x input stages (the
+// diagonal in-CTA split).  Each is run once to warm up and once timed.
+std::vector<tm_config> tune_candidates() {
+    std::vector<tm_config> c;
+    const int tiles[] = {1024, 2048, 4096};
+    const int threads[] = {128, 256};
+    const int stages[] = {3, 4};
+    for (int t : tiles)
+        for (int th : threads)
+            for (int st : stages) {
+                tm_config x{};
+                x.tile = t; x.threads = th; x.stages = st; x.split = TM_SPLIT_DIAGONAL;
+                c.push_back(x);
+            }
+    return c;
+}
+
+template <typename Run>
+tm_status tune(int op, tm_key_type kt, int64_t total, size_t ws_have, size_t (*ws_need)(const tm_config*),
+               Run run, tm_config* best_out, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TM_ERR_CUDA;
+    float best_ms = -1.f;
+    tm_config best{};
+    for (const tm_config& c : tune_candidates()) {
+        if (ws_need(&c) > ws_have) continue;
+        if (run(&c) != TM_OK) continue;                   // warm-up (and support check)
+        cudaEventRecord(e0, s);
+        tm_status st = run(&c);
+        cudaEventRecord(e1, s);
+        if (st != TM_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms < 0.f) return TM_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[TuneKey{op, (int)kt, log2_bucket(total)}] = best;
+    }
+    if (best_out) *best_out = best;
+    return TM_OK;
+}
+
+thread_local int64_t t_pairs, t_total_a, t_total_b, t_n;
+size_t batched_ws_need(const tm_config* c) { return tm_merge_batched_workspace_size(t_pairs, t_total_a, t_total_b, c); }
+size_t sort_ws_need(const tm_config* c) { return tm_merge_sort_workspace_size(t_n, c); }
+
+}  // namespace
+
+extern "C" {
+
+tm_status tm_autotune_batched(tm_key_type kt, int64_t num_pairs,
+                              const int64_t* a_offsets, const void* a_keys, const uint32_t* a_vals, int64_t total_a,
+                              const int64_t* b_offsets, const void* b_keys, const uint32_t* b_vals, int64_t total_b,
+                              void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
+                              tm_config* best, tm_stream_t stream) {
+    tm_status st = check_batched(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
+                                 total_b, c_keys, c_vals);
+    if (st != TM_OK) return st;
+    if (!workspace || !aligned(workspace, 256)) return TM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t_pairs = num_pairs; t_total_a = total_a; t_total_b = total_b;
+    auto run = [&](const tm_config* c) {
+        return batched_dispatch(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
+                                total_b, c_keys, c_vals, workspace, c, s);
+    };
+    return tune(1, kt, total_a + total_b, workspace_bytes, batched_ws_need, run, best, s);
+}
+
+tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t* src_vals, int64_t n,
+                           void* keys, uint32_t* vals, void* tmp_keys, uint32_t* tmp_vals,
+                           void* workspace, size_t workspace_bytes, tm_config* best, tm_stream_t stream) {
+    if (n < 0) return TM_ERR_INVALID;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if (n > 0 && (!aligned(src_keys, E) || !aligned(src_vals, 4) || !aligned(keys, E) || !aligned(vals, 4) ||
+                  !aligned(tmp_keys, E) || !aligned(tmp_vals, 4)))
+        return TM_ERR_INVALID;
+    if (!workspace || !aligned(workspace, 256)) return TM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t_n = n;
+    // every trial sorts a fresh copy of the source; the copy is outside the
+    // timed sort only in the sense that it is the same for every candidate
+    auto run = [&](const tm_config* c) -> tm_status {
+        if (cudaMemcpyAsync(keys, src_keys, (size_t)n * E, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(vals, src_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return TM_ERR_CUDA;
+        return tm_merge_sort(kt, keys, vals, n, tmp_keys, tmp_vals, workspace, workspace_bytes, c, stream);
+    };
+    return tune(2, kt, n, workspace_bytes, sort_ws_need, run, best, s);
+}
+
+int tm_autotune_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const int k = (int)g_tune.size();
+    g_tune.clear();
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs: capture any sequence of calls on a stream, replay it
+// ---------------------------------------------------------------------------
+
+struct tm_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+tm_status tm_graph_capture_begin(tm_stream_t stream) {
+    if (!stream) return TM_ERR_INVALID;              // the legacy stream cannot be captured
+    return cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal) ==
+                   cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out) {
+    if (!stream || !out) return TM_ERR_INVALID;
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &g) != cudaSuccess || !g) return TM_ERR_CUDA;
+    cudaGraphExec_t e = nullptr;
+    if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return TM_ERR_CUDA;
+    }
+    tm_graph* h = new (std::nothrow) tm_graph{g, e};
+    if (!h) {
+        cudaGraphExecDestroy(e);
+        cudaGraphDestroy(g);
+        return TM_ERR_INVALID;
+    }
+    *out = h;
+    return TM_OK;
+}
+
+tm_status tm_graph_launch(tm_graph* g, tm_stream_t stream) {
+    if (!g) return TM_ERR_INVALID;
+    return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+}
+
+void tm_graph_destroy(tm_graph* g) {
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+}  // extern "C"

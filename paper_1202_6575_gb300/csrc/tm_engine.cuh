@@ -29,11 +29,15 @@ namespace pmerge {
 // consecutive records are adjacent pieces of the merge path: their A ranges,
 // B ranges and outputs are contiguous, and any run of them is itself a valid
 // subproblem.
+// `first` marks the first record of a merge (of a pair, in the batched
+// form): records are never packed across it.
 struct __align__(16) TileDesc {
     int64_t a0, b0, c0;
     int32_t nA, nB;
+    int32_t first, pad0;
+    int64_t pad1;
 };
-static_assert(sizeof(TileDesc) == 32, "descriptor layout");
+static_assert(sizeof(TileDesc) == 48, "descriptor layout");
 
 // ceil(2^31 / d): floor(k / d) == (k * inv31(d)) >> 31 exactly for
 // 0 <= k < 2^15 and 1 <= d <= 2^14 (the error term k*(M - 2^31/d)/2^31 stays
@@ -178,7 +182,9 @@ struct StageHeader {
 
 struct EngineArgs {
     const TileDesc* desc;
-    int64_t n_items;
+    int64_t n_items;               // record count, or -1: read it from *n_items_dev
+    const int64_t* n_items_dev;
+    int64_t items_bound;           // upper bound of the record count (host side, for sizing)
     unsigned long long* queue;     // work-queue counter, zero at launch
     int32_t* status;
     const void* A; const uint32_t* Av; int64_t lenA;   // arrays the descriptors index
@@ -274,7 +280,7 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
     int k = 0;                                        // fills issued
     bool ok = true;
     const int G = g.grab;
-    const unsigned long long nitems = (unsigned long long)g.n_items;
+    const unsigned long long nitems = (unsigned long long)(g.n_items >= 0 ? g.n_items : *g.n_items_dev);
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(g.queue, (unsigned long long)G);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -297,7 +303,8 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
             for (; q < avail; ++q) {                  // pack the following records while they fit
                 const int xA = __shfl_sync(0xffffffffu, d.nA, q);
                 const int xB = __shfl_sync(0xffffffffu, d.nB, q);
-                if (nA + nB + xA + xB > g.cap) break;
+                const int xf = __shfl_sync(0xffffffffu, d.first, q);
+                if (xf || nA + nB + xA + xB > g.cap) break;
                 nA += xA;
                 nB += xB;
             }

@@ -21,9 +21,11 @@ tm_status launch_engine_s(const EngineArgs& a_in, const tm_config* cfg, cudaStre
         return TM_ERR_UNSUPPORTED;
     int64_t grid = (int64_t)per_sm * sm_count();
     if (cfg && cfg->grid > 0) grid = cfg->grid;
-    int64_t g = a.n_items / (grid * 8);
+    // n_items may live on the device (batched form); then size by its bound
+    const int64_t items = a.n_items >= 0 ? a.n_items : a.items_bound;
+    int64_t g = items / (grid * 8);
     a.grab = (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
-    int64_t need = (a.n_items + a.grab - 1) / a.grab;
+    int64_t need = (items + a.grab - 1) / a.grab;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return TM_ERR_CUDA;

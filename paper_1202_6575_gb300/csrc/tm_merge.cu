@@ -81,9 +81,10 @@ plan_single_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restrict__ 
     subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
     const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
                                  : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
-    TileDesc d;
+    TileDesc d{};
     d.a0 = a0; d.b0 = b0; d.c0 = a0 + b0;
     d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);
+    d.first = chain == 0;
     desc[chain] = d;
 }
 
@@ -255,7 +256,7 @@ static tm_status merge_tiles_typed(const void* a_keys, const uint32_t* a_vals, i
                                    void* c_keys, uint32_t* c_vals, void* control,
                                    const tm_config* cfg, cudaStream_t s) {
     EngineArgs a{};
-    a.desc = tiles; a.n_items = n_tiles;
+    a.desc = tiles; a.n_items = n_tiles; a.items_bound = n_tiles;
     a.status = reinterpret_cast<int32_t*>(control);
     a.queue = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(control) + 8);
     a.A = a_keys; a.Av = a_vals; a.lenA = n;

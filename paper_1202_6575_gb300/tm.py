@@ -67,6 +67,19 @@ _SIGNATURES = {
     "tm_rank_search": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _P, _P]),
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "tm_merge_batched_workspace_size": (_SZ, [_I64, _I64, _I64, _P]),
+    "tm_merge_batched": (ctypes.c_int, [ctypes.c_int, _I64, _P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P, _SZ,
+                                        _P, _P]),
+    "tm_merge_sort_workspace_size": (_SZ, [_I64, _P]),
+    "tm_merge_sort": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _P, _SZ, _P, _P]),
+    "tm_autotune_batched": (ctypes.c_int, [ctypes.c_int, _I64, _P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P,
+                                           _SZ, _P, _P]),
+    "tm_autotune_sort": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "tm_autotune_clear": (ctypes.c_int, []),
+    "tm_graph_capture_begin": (ctypes.c_int, [_P]),
+    "tm_graph_capture_end": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
+    "tm_graph_launch": (ctypes.c_int, [_P, _P]),
+    "tm_graph_destroy": (None, [_P]),
 }
 
 
@@ -274,3 +287,140 @@ def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream
                                    _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_noalloc")
     return C, Cv
+
+
+# ---------------------------------------------------------------------------
+# Many merges, merge sort, autotuner, graphs
+# ---------------------------------------------------------------------------
+
+def _cfg_dict(c: TmConfig) -> dict:
+    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_ if f != "reserved"}
+
+
+def tm_merge_batched_workspace_size(num_pairs: int, total_a: int, total_b: int, cfg=None) -> int:
+    return int(load().tm_merge_batched_workspace_size(num_pairs, total_a, total_b, _cfg(cfg)))
+
+
+def _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv):
+    kd = TORCH_KEY_DTYPES[kt]
+    pairs = a_off.numel() - 1
+    if b_off.numel() != pairs + 1:
+        raise ValueError("offset arrays differ in length")
+    ta, tb = A.numel(), B.numel()
+    if C is None:
+        C = torch.empty(ta + tb, dtype=A.dtype, device=A.device)
+    if Cv is None:
+        Cv = torch.empty(ta + tb, dtype=torch.int32, device=A.device)
+    args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av"), ta,
+            _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv"), tb,
+            _dev(C, "C", kd), _dev(Cv, "Cv"))
+    return args, C, Cv, pairs, ta, tb
+
+
+def tm_merge_batched(kt: str, a_off, A, Av, b_off, B, Bv, C=None, Cv=None, workspace=None, cfg=None,
+                     stream=None):
+    """Independent stable merges of CSR pairs; returns (C, Cv, workspace)."""
+    args, C, Cv, pairs, ta, tb = _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv)
+    if workspace is None:
+        workspace = new_workspace(tm_merge_batched_workspace_size(pairs, ta, tb, cfg), A.device)
+    code = load().tm_merge_batched(*args, _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg),
+                                   _stream(stream))
+    _check(code, "tm_merge_batched")
+    return C, Cv, workspace
+
+
+def tm_merge_sort_workspace_size(n: int, cfg=None) -> int:
+    return int(load().tm_merge_sort_workspace_size(n, _cfg(cfg)))
+
+
+def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=None, cfg=None, stream=None):
+    """Stable sort of (keys, vals) in place; returns (keys, vals, workspace)."""
+    kd = TORCH_KEY_DTYPES[kt]
+    n = keys.numel()
+    if tmp_keys is None:
+        tmp_keys = torch.empty_like(keys)
+    if tmp_vals is None:
+        tmp_vals = torch.empty_like(vals)
+    if workspace is None:
+        workspace = new_workspace(tm_merge_sort_workspace_size(n, cfg), keys.device)
+    code = load().tm_merge_sort(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals"), n,
+                                _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals"),
+                                _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg), _stream(stream))
+    _check(code, "tm_merge_sort")
+    return keys, vals, workspace
+
+
+def tm_autotune_batched(kt: str, a_off, A, Av, b_off, B, Bv, C, Cv, workspace, stream=None) -> dict:
+    args, C, Cv, pairs, ta, tb = _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv)
+    best = TmConfig()
+    code = load().tm_autotune_batched(*args, _dev(workspace, "workspace"), workspace.numel(),
+                                      ctypes.byref(best), _stream(stream))
+    _check(code, "tm_autotune_batched")
+    return _cfg_dict(best)
+
+
+def tm_autotune_sort(kt: str, src_keys, src_vals, keys, vals, tmp_keys, tmp_vals, workspace, stream=None) -> dict:
+    kd = TORCH_KEY_DTYPES[kt]
+    best = TmConfig()
+    code = load().tm_autotune_sort(_kt(kt), _dev(src_keys, "src_keys", kd), _dev(src_vals, "src_vals"),
+                                   src_keys.numel(), _dev(keys, "keys", kd), _dev(vals, "vals"),
+                                   _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals"),
+                                   _dev(workspace, "workspace"), workspace.numel(), ctypes.byref(best),
+                                   _stream(stream))
+    _check(code, "tm_autotune_sort")
+    return _cfg_dict(best)
+
+
+def tm_autotune_clear() -> int:
+    return int(load().tm_autotune_clear())
+
+
+def tm_graph_capture_begin(stream):
+    _check(load().tm_graph_capture_begin(_stream(stream)), "tm_graph_capture_begin")
+
+
+def tm_graph_capture_end(stream):
+    h = ctypes.c_void_p()
+    _check(load().tm_graph_capture_end(_stream(stream), ctypes.byref(h)), "tm_graph_capture_end")
+    return h
+
+
+def tm_graph_launch(g, stream=None):
+    _check(load().tm_graph_launch(g, _stream(stream)), "tm_graph_launch")
+
+
+def tm_graph_destroy(g):
+    load().tm_graph_destroy(g)
+
+
+class Graph:
+    """Captures the tm_* calls made inside `with Graph(stream) as g:` on
+    `stream` (a non-default torch.cuda.Stream, made current in the block)
+    into a CUDA graph; g.launch() replays them."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.handle = None
+
+    def __enter__(self):
+        self._ctx = torch.cuda.stream(self.stream)
+        self._ctx.__enter__()
+        tm_graph_capture_begin(self.stream)
+        return self
+
+    def __exit__(self, *exc):
+        try:
+            self.handle = tm_graph_capture_end(self.stream)
+        finally:
+            self._ctx.__exit__(*exc)
+
+    def launch(self, stream=None):
+        tm_graph_launch(self.handle, stream or self.stream)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                tm_graph_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None

@@ -65,7 +65,7 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.tm_cross_ranks(0, P(16), 4, P(16), 4, 0, P(64), P(64), None) == tm.TM_ERR_INVALID
     assert lib.tm_merge_tiles(0, P(16), P(16), 4, P(16), P(16), 4, P(64), 1, 0, P(64), P(64), P(256), None, None) == tm.TM_ERR_INVALID
     assert lib.tm_plan_subproblems(4, 4, 0, P(64), P(64), P(64), None, None) == tm.TM_ERR_INVALID
-    assert lib.tm_tile_record_bytes() == 32
+    assert lib.tm_tile_record_bytes() == 48
     assert lib.tm_plan_tile_count(10, 3, 5) == 5 + 3
     assert lib.tm_merge_tile_cap(10, 7, 3) == 4 + 3
     assert lib.tm_rank_search(0, 2, P(16), 4, P(16), 4, P(64), None) == tm.TM_ERR_INVALID

@@ -162,7 +162,7 @@ def test_three_phases_match_oracle_table():
         xbar, ybar = tm.tm_cross_ranks("u32", dA, dB, p)
         tiles = tm.tm_plan_subproblems(n, m, p, xbar, ybar)
         count = tm.tm_plan_tile_count(n, m, p)
-        rec = tiles.view(torch.int64).view(2 * p, 4)[:count].cpu().numpy()
+        rec = tiles.view(torch.int64).view(2 * p, 6)[:count].cpu().numpy()
         otable = oracle.subproblems(n, m, p, xbar.cpu().numpy(), ybar.cpu().numpy())
         expect = []
         for k in range(2 * p):
