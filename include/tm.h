@@ -274,6 +274,90 @@ TM_API tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out);
 TM_API tm_status tm_graph_launch(tm_graph* g, tm_stream_t stream);
 TM_API void tm_graph_destroy(tm_graph* g);
 
+/* ------------------------------------------------------------------------ */
+/* Learned cross-rank proposal (not in the paper)                            */
+/* ------------------------------------------------------------------------ */
+
+/* A model of the distribution of a large sorted float32 base array X that is
+ * merged again and again with incoming sorted batches (base' = merge(base,
+ * batch), base on the A side so that older keys win ties).  It proposes the
+ * cross ranks of Steps 1-2; every proposal is searched only in a window and
+ * then checked against the definition of rank_low / rank_high (Section 2);
+ * a failed check runs the full binary search, so results never depend on
+ * the model.
+ *
+ * Model: S segments with knot keys K[s] = X[floor(s N / S)] (K[S] = X[N-1])
+ * and their ranks R[s] in the current base (a piecewise-linear CDF), plus a
+ * two-layer MLP (2 inputs, H ReLU units, 1 output) that predicts the
+ * residual of the piecewise-linear rank in units of the segment's size, from
+ * the key's position t in its segment and the segment index.  The error
+ * bound eps (calibrated, in segment units) sets the search window.  Training
+ * is full-batch Adam on (key, exact rank_high) pairs.
+ *
+ * Memory: one caller-owned device buffer of tm_cdf_model_bytes(S, H) bytes
+ * (256-byte aligned).  Layout, little endian: a 256-byte header
+ *   int32 S; int32 H; float eps; int32 cur; int64 N; uint64 fallbacks;
+ *   uint64 learned_searches; int64 adam_steps; float loss; int32 pad;
+ * then, each section starting on a 256-byte boundary: float K[S+1];
+ * int64 R0[S+1]; int64 R1[S+1] (R_cur is R0 when cur = 0); float params[4H+1]
+ * = W1 (H x 2, row major), b1 (H), w2 (H), b2; float adam_m[4H+1];
+ * float adam_v[4H+1]; float grad[4H+1]; float eps_seg[S] (per-segment error
+ * bound, 0 for a segment without labels).  Every call takes the model's S
+ * and H; none reads the header back, so all of them can be graph-captured. */
+enum { TM_LEARNED_ADVANCE = 1 };
+
+TM_API size_t tm_cdf_model_bytes(int segments, int hidden);
+
+/* Knots from the base (n sorted keys), parameters from init_params (device,
+ * 4H+1 floats), Adam state zeroed, N = n. */
+TM_API tm_status tm_cdf_init(void* model, int segments, int hidden, const float* base_keys, int64_t n,
+                             const float* init_params, tm_stream_t stream);
+
+/* Gradient (device, 4H+1 floats) and loss (device float) of the mean
+ * 0.5 * (y - tau)^2 over `count` labelled keys, at the current parameters;
+ * no update.  labels: exact rank_high of q in the base (int64). */
+TM_API tm_status tm_cdf_grad(void* model, int segments, int hidden, const float* q, const int64_t* labels,
+                             int64_t count, float* grad_out, float* loss_out, tm_stream_t stream);
+
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate
+ * lr) on the labelled keys: one forward+backward kernel and one update
+ * kernel per step. */
+TM_API tm_status tm_cdf_train(void* model, int segments, int hidden, const float* q, const int64_t* labels,
+                              int64_t count, int steps, float lr, tm_stream_t stream);
+
+/* Predicted rank (float) of every key. */
+TM_API tm_status tm_cdf_predict(const void* model, int segments, int hidden, const float* q, int64_t count,
+                                float* pred, tm_stream_t stream);
+
+/* eps = max |y - tau| over the labelled keys (segment units), and per
+ * segment the same maximum over the labels falling in it. */
+TM_API tm_status tm_cdf_calibrate(void* model, int segments, int hidden, const float* q, const int64_t* labels,
+                                  int64_t count, tm_stream_t stream);
+
+/* Steps 1-2 with learned proposals: A = the model's current base (n keys),
+ * B = a batch (m keys), p blocks; same results as tm_cross_ranks.  B-block
+ * starts search A in [pred - eps*scale - 2, pred + eps*scale + 2]; A-block
+ * starts search B around the model's CDF scaled to m, with that window
+ * scaled to m and widened by 4 sqrt(m) for B's own sampling error.  With TM_LEARNED_ADVANCE in
+ * flags the knot ranks of merge(A, B) are written to the other rank buffer
+ * (R'[s] = R[s] + rank_low(K[s], B), searched the same way as the A-block
+ * starts) and made current, and N becomes n + m: the model then describes
+ * the merged base.  Windows: B-block starts search the base within
+ * 2 eps_s * (segment size) + 16 ranks of the proposal, eps_s the error bound
+ * of the key's segment (the global one when the segment had no labels).
+ * Counts of learned searches and of fallbacks accumulate in the header. */
+TM_API tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const float* a_keys, int64_t n,
+                                        const float* b_keys, int64_t m, int64_t p, int64_t* xbar, int64_t* ybar,
+                                        int flags, tm_stream_t stream);
+
+/* tm_merge for float keys with the learned Steps 1-2 (same workspace as
+ * tm_merge; same result). */
+TM_API tm_status tm_merge_learned(void* model, int segments, int hidden,
+                                  const float* a_keys, const uint32_t* a_vals, int64_t n,
+                                  const float* b_keys, const uint32_t* b_vals, int64_t m,
+                                  float* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
+                                  const tm_config* cfg, int flags, tm_stream_t stream);
+
 /* Stable merge that allocates nothing and needs no workspace.  The paper has
  * no counterpart; this is a convenience of the library.  It exists for
  * callers that cannot call cudaMalloc or hand the library a workspace: code

@@ -80,6 +80,17 @@ _SIGNATURES = {
     "tm_graph_capture_end": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
     "tm_graph_launch": (ctypes.c_int, [_P, _P]),
     "tm_graph_destroy": (None, [_P]),
+    "tm_cdf_model_bytes": (_SZ, [ctypes.c_int, ctypes.c_int]),
+    "tm_cdf_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _P]),
+    "tm_cdf_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _I64, _P, _P, _P]),
+    "tm_cdf_train": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _I64, ctypes.c_int, ctypes.c_float,
+                                    _P]),
+    "tm_cdf_predict": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _P]),
+    "tm_cdf_calibrate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _I64, _P]),
+    "tm_cross_ranks_learned": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _I64, _P, _P,
+                                              ctypes.c_int, _P]),
+    "tm_merge_learned": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P,
+                                        _SZ, _P, ctypes.c_int, _P]),
 }
 
 
@@ -424,3 +435,111 @@ class Graph:
             except Exception:
                 pass
             self.handle = None
+
+
+# ---------------------------------------------------------------------------
+# Learned cross-rank proposal
+# ---------------------------------------------------------------------------
+
+LEARNED_ADVANCE = 1
+
+
+class CdfModel:
+    """A learned CDF model in a device buffer (layout in include/tm.h)."""
+
+    HEADER = [("S", "<i4", 0), ("H", "<i4", 4), ("eps", "<f4", 8), ("cur", "<i4", 12), ("N", "<i8", 16),
+              ("fallbacks", "<u8", 24), ("learned", "<u8", 32), ("adam_steps", "<i8", 40), ("loss", "<f4", 48)]
+
+    def __init__(self, segments: int, hidden: int, device):
+        self.S, self.H = int(segments), int(hidden)
+        nbytes = int(load().tm_cdf_model_bytes(self.S, self.H))
+        if nbytes == 0:
+            raise ValueError("bad model dimensions")
+        self.buf = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+        self.P = 4 * self.H + 1
+
+    def _p(self):
+        return _dev(self.buf, "model")
+
+    def init(self, base, init_params, stream=None):
+        ip = init_params.to(device=self.buf.device, dtype=torch.float32).contiguous()
+        _check(load().tm_cdf_init(self._p(), self.S, self.H, _dev(base, "base", (torch.float32,)), base.numel(),
+                                  _dev(ip, "init_params"), _stream(stream)), "tm_cdf_init")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return self
+
+    def grad(self, q, labels, stream=None):
+        g = torch.empty(self.P, dtype=torch.float32, device=self.buf.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.buf.device)
+        _check(load().tm_cdf_grad(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)),
+                                  _dev(labels, "labels", (torch.int64,)), q.numel(), _dev(g, "g"), _dev(loss, "loss"),
+                                  _stream(stream)), "tm_cdf_grad")
+        return g, loss
+
+    def train(self, q, labels, steps: int, lr: float, stream=None):
+        _check(load().tm_cdf_train(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)),
+                                   _dev(labels, "labels", (torch.int64,)), q.numel(), int(steps), float(lr),
+                                   _stream(stream)), "tm_cdf_train")
+
+    def predict(self, q, stream=None):
+        out = torch.empty(q.numel(), dtype=torch.float32, device=q.device)
+        _check(load().tm_cdf_predict(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)), q.numel(),
+                                     _dev(out, "pred"), _stream(stream)), "tm_cdf_predict")
+        return out
+
+    def calibrate(self, q, labels, stream=None):
+        _check(load().tm_cdf_calibrate(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)),
+                                       _dev(labels, "labels", (torch.int64,)), q.numel(), _stream(stream)),
+               "tm_cdf_calibrate")
+
+    def _section(self, idx: int, dtype, count: int):
+        # sections after the 256-byte header, each 256-byte aligned: K, R0, R1, params, m, v, grad, eps_seg
+        sizes = [(self.S + 1) * 4, (self.S + 1) * 8, (self.S + 1) * 8] + [self.P * 4] * 4 + [self.S * 4]
+        off = 256 + sum((x + 255) // 256 * 256 for x in sizes[:idx])
+        return self.buf[off:off + count * torch.tensor([], dtype=dtype).element_size()].view(dtype)
+
+    def knots(self):
+        return self._section(0, torch.float32, self.S + 1)
+
+    def ranks(self, which: int):
+        return self._section(1 + which, torch.int64, self.S + 1)
+
+    def params(self):
+        return self._section(3, torch.float32, self.P)
+
+    def eps_segments(self):
+        return self._section(7, torch.float32, self.S)
+
+    def header(self) -> dict:
+        import numpy as np
+        raw = self.buf[:64].cpu().numpy()
+        return {name: np.frombuffer(raw[off:off + np.dtype(dt).itemsize].tobytes(), dtype=dt)[0].item()
+                for name, dt, off in self.HEADER}
+
+
+def tm_cross_ranks_learned(model: CdfModel, A, B, p: int, xbar=None, ybar=None, flags: int = 0, stream=None):
+    if xbar is None:
+        xbar = torch.empty(p + 1, dtype=torch.int64, device=A.device)
+    if ybar is None:
+        ybar = torch.empty(p + 1, dtype=torch.int64, device=A.device)
+    _check(load().tm_cross_ranks_learned(model._p(), model.S, model.H, _dev(A, "A", (torch.float32,)), A.numel(),
+                                         _dev(B, "B", (torch.float32,)), B.numel(), p,
+                                         _dev(xbar, "xbar", (torch.int64,)), _dev(ybar, "ybar", (torch.int64,)),
+                                         int(flags), _stream(stream)), "tm_cross_ranks_learned")
+    return xbar, ybar
+
+
+def tm_merge_learned(model: CdfModel, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, flags: int = 0,
+                     stream=None):
+    n, m = A.numel(), B.numel()
+    if C is None:
+        C = torch.empty(n + m, dtype=torch.float32, device=A.device)
+    if Cv is None:
+        Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
+    if workspace is None:
+        workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)
+    _check(load().tm_merge_learned(model._p(), model.S, model.H, _dev(A, "A", (torch.float32,)), _dev(Av, "Av"), n,
+                                   _dev(B, "B", (torch.float32,)), _dev(Bv, "Bv"), m,
+                                   _dev(C, "C", (torch.float32,)), _dev(Cv, "Cv"), _dev(workspace, "workspace"),
+                                   workspace.numel(), _cfg(cfg), int(flags), _stream(stream)), "tm_merge_learned")
+    return C, Cv, workspace
