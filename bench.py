@@ -314,6 +314,106 @@ def bench_sort(dev, steps: int = 3):
             "frac_of_hbm": moved / (ms / 1e3) / 1e9 / measured_peaks()[0]}
 
 
+def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int = 20):
+    """LSM-style repeated merging: a sorted float32 base of 2**28 keys (3
+    lognormals, mu 0/2/5, sigma 0.5) merged `merges` times with sorted
+    batches of 2**20 keys from the same mixture (the base on the A side).
+    Plain form: tm_cross_ranks + plan + tile merge per merge.  Learned form:
+    the model (4096 segments + MLP 2-64-1) trained on 2**18 exact rank_high
+    labels from the plain search, then tm_cross_ranks_learned (advancing the
+    knot ranks) + plan + tile merge per merge.  Both end in bit-identical
+    bases."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    N0, m = 1 << log2_base, 1 << log2_batch
+    cap = N0 + merges * m
+    X0, X0v = W.lsm_base(dev, n=N0)
+    batches = [W.lsm_batch(k, dev, size=m, base_n=N0) for k in range(merges)]
+    bufs = [(torch.empty(cap, dtype=torch.float32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev))
+            for _ in range(2)]
+    p_max = tm.tm_merge_blocks(cap, m)
+    xbar = torch.empty(p_max + 1, dtype=torch.int64, device=dev)
+    ybar = torch.empty(p_max + 1, dtype=torch.int64, device=dev)
+    tiles = torch.empty(2 * p_max * tm.tm_tile_record_bytes(), dtype=torch.uint8, device=dev)
+    control = torch.zeros(256, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+
+    def run(search):
+        bufs[0][0][:N0].copy_(X0)
+        bufs[0][1][:N0].copy_(X0v)
+        torch.cuda.synchronize(dev)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(merges)]
+        n = N0
+        src = 0
+        for k in range(merges):
+            A, Av = bufs[src][0][:n], bufs[src][1][:n]
+            B, Bv = batches[k]
+            C, Cv = bufs[src ^ 1][0][:n + m], bufs[src ^ 1][1][:n + m]
+            p = tm.tm_merge_blocks(n, m)
+            ev[k][0].record(s)
+            search(A, B, p)
+            ev[k][1].record(s)
+            tm.tm_plan_subproblems(n, m, p, xbar, ybar, tiles, stream=s)
+            tm.tm_merge_tiles("f32", A, Av, B, Bv, tiles, tm.tm_plan_tile_count(n, m, p),
+                              tm.tm_merge_tile_cap(n, m, p), C, Cv, control, stream=s)
+            ev[k][2].record(s)
+            n += m
+            src ^= 1
+        ev[-1][2].synchronize()
+        assert tm.tm_read_status(control, stream=s) == 0
+        total_ms = ev[0][0].elapsed_time(ev[-1][2])
+        search_ms = [e[0].elapsed_time(e[1]) for e in ev]
+        return total_ms, search_ms, src, n
+
+    def plain(A, B, p):
+        tm.tm_cross_ranks("f32", A, B, p, xbar, ybar, stream=s)
+
+    run(plain)                                       # warm-up
+    t_plain, srch_plain, src, n_final = run(plain)
+    ref = bufs[src][0][:n_final].clone(), bufs[src][1][:n_final].clone()
+
+    # model: trained on exact ranks of 2**18 mixture keys in the initial base
+    t0 = time.perf_counter()
+    q = W.lsm_label_keys(dev, count=1 << 18)
+    labels = tm.tm_rank_search("f32", "high", q, X0)
+    init = W.cdf_init(hidden=64)
+    flat = torch.cat([init["W1"].reshape(-1), init["b1"], init["w2"], init["b2"].reshape(1)])
+    model = tm.CdfModel(4096, 64, dev).init(X0, flat)
+    model.train(q, labels, steps=400, lr=3e-3)
+    qc = W.lsm_label_keys(dev, count=1 << 20, seed=W.SEED_BASE + 8)
+    model.calibrate(qc, tm.tm_rank_search("f32", "high", qc, X0))
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    init_state = model.buf.clone()
+
+    def learned(A, B, p):
+        tm.tm_cross_ranks_learned(model, A, B, p, xbar, ybar, flags=tm.LEARNED_ADVANCE, stream=s)
+
+    model.buf.copy_(init_state)
+    run(learned)                                     # warm-up (advances the knot ranks)
+    model.buf.copy_(init_state)
+    torch.cuda.synchronize(dev)
+    t_learned, srch_learned, src, n_final = run(learned)
+    same = torch.equal(bufs[src][0][:n_final], ref[0]) and torch.equal(bufs[src][1][:n_final], ref[1])
+    h = model.header()
+    elems = sum(N0 + k * m + m for k in range(merges))
+    seg = (N0 + merges * m / 2) / 4096
+    eps_s = model.eps_segments().cpu().numpy()
+    return {"workload": f"base 2^{log2_base} f32 (3 lognormals) merged {merges} times with sorted 2^{log2_batch} "
+                        "batches; u32 payloads",
+            "elements": elems,
+            "plain": {"value": elems / (t_plain / 1e3), "unit": UNIT, "ms_total": t_plain,
+                      "search_ms_mean": float(np.mean(srch_plain))},
+            "learned": {"value": elems / (t_learned / 1e3), "unit": UNIT, "ms_total": t_learned,
+                        "search_ms_mean": float(np.mean(srch_learned)),
+                        "fallbacks": int(h["fallbacks"]), "learned_searches": int(h["learned"]),
+                        "mean_window_probes": float(np.mean(np.log2(2 * (3 * eps_s * seg + 32) + 1))),
+                        "plain_probes": float(np.log2(N0 + merges * m / 2)),
+                        "train_seconds_once": train_s},
+            "search_speedup": float(np.mean(srch_plain) / np.mean(srch_learned)),
+            "end_to_end_speedup": t_plain / t_learned,
+            "bit_identical": bool(same)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,13 +430,31 @@ def main():
     ap.add_argument("--dists", default="", help="comma list of distributions (default: all four)")
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the batched and merge-sort forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
+    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned"],
+                    help="run one form alone (profiling)")
+    ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
+    ap.add_argument("--log2-base", type=int, default=28, help="learned form: base size (profiling)")
     args = ap.parse_args()
     args.dists = [d for d in args.dists.split(",") if d] or None
     rank, local_rank, world = env_rank()
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+
+    if args.form:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        import __graft_entry__
+        __graft_entry__.build()
+        if args.form == "batched":
+            out = bench_batched(dev)
+        elif args.form == "sort":
+            out = bench_sort(dev)
+        else:
+            out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
+        print(json.dumps({"form": args.form, **out}), flush=True)
         return
 
     import torch.distributed as dist
@@ -500,6 +618,8 @@ def main():
             it.clear()
         torch.cuda.empty_cache()
         forms = {"batched": bench_batched(dev), "merge_sort": bench_sort(dev)}
+        torch.cuda.empty_cache()
+        forms["learned"] = bench_learned(dev)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,

@@ -335,17 +335,16 @@ TM_API tm_status tm_cdf_calibrate(void* model, int segments, int hidden, const f
                                   int64_t count, tm_stream_t stream);
 
 /* Steps 1-2 with learned proposals: A = the model's current base (n keys),
- * B = a batch (m keys), p blocks; same results as tm_cross_ranks.  B-block
- * starts search A in [pred - eps*scale - 2, pred + eps*scale + 2]; A-block
- * starts search B around the model's CDF scaled to m, with that window
- * scaled to m and widened by 4 sqrt(m) for B's own sampling error.  With TM_LEARNED_ADVANCE in
+ * B = a batch (m keys), p blocks; same results as tm_cross_ranks.  The
+ * B-block starts, which search the large base, use the model: each searches
+ * the base within 3 eps_s * (segment size) + 32 ranks of the proposal (eps_s
+ * the calibrated error of the key's segment, the global one when the
+ * segment had no labels), and the answer is verified.  The A-block starts
+ * search the small batch by plain bisection.  With TM_LEARNED_ADVANCE in
  * flags the knot ranks of merge(A, B) are written to the other rank buffer
- * (R'[s] = R[s] + rank_low(K[s], B), searched the same way as the A-block
- * starts) and made current, and N becomes n + m: the model then describes
- * the merged base.  Windows: B-block starts search the base within
- * 2 eps_s * (segment size) + 16 ranks of the proposal, eps_s the error bound
- * of the key's segment (the global one when the segment had no labels).
- * Counts of learned searches and of fallbacks accumulate in the header. */
+ * (R'[s] = R[s] + rank_low(K[s], B)) and made current, and N becomes n + m:
+ * the model then describes the merged base.  Counts of learned searches and
+ * of fallbacks accumulate in the header. */
 TM_API tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const float* a_keys, int64_t n,
                                         const float* b_keys, int64_t m, int64_t p, int64_t* xbar, int64_t* ybar,
                                         int flags, tm_stream_t stream);

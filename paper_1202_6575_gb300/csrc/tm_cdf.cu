@@ -286,65 +286,114 @@ __device__ __forceinline__ bool windowed_rank(const float* __restrict__ X, int64
     return false;
 }
 
-// Window half-width (ranks of the base) for a key in segment s: twice the
-// segment's calibrated error (the global one when the segment saw no
-// labels), in ranks, plus a margin.
-__device__ __forceinline__ double base_window(const CdfView& mv, const CdfPoint& c, float eps_global) {
-    float e = mv.eps_seg[c.s];
-    if (!(e > 0.f)) e = eps_global;
-    return 2.0 * (double)e * c.scale + 16.0;
+// ---------------------------------------------------------------------------
+// Search-side evaluation of the model, in float32 and integer arithmetic
+// only (no float64 on the search path): the proposal is r0 + off with
+// r0 = R[s] exact and off = t * seg + y * max(seg, 1) a float offset.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int seg_smem(const float* K, int S, float q) {
+    int lo = 0, len = S - 1;                           // knots K[1..S-1] <= q
+    const float* X = K + 1;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (!(q < X[lo + half])) { lo += half + 1; len -= half + 1; } else { len = half; }
+    }
+    return lo;
 }
 
-// Proposed rank of `key` in a batch of m keys drawn from the base's
-// distribution (the base CDF scaled to m) and the window for it: the model's
-// window scaled to m plus 4 sqrt(m) for the batch's own sampling deviation
-// (a binomial count has standard deviation at most sqrt(m)/2).
-__device__ __forceinline__ void batch_window(const CdfView& mv, const float* p, const int64_t* R, float key,
-                                             double N, int64_t m, float eps, int64_t& lo, int64_t& hi) {
-    const CdfPoint c = cdf_point(mv.K, R, mv.S, key);
-    const double f = (double)m / N;
-    const double pred = (c.pla + (double)cdf_mlp(p, mv.H, c.f0, c.f1) * c.scale) * f;
-    const double w = base_window(mv, c, eps) * f + 4.0 * sqrt((double)m) + 2.0;
-    lo = (int64_t)fmax(0.0, floor(pred - w));
-    hi = (int64_t)fmin((double)m, ceil(pred + w));
+__device__ __forceinline__ float mlp_ilp(const float* p, int H, float f0, float f1) {
+    const float* W1 = p;
+    const float* b1 = p + 2 * H;
+    const float* w2 = p + 3 * H;
+    float y0 = p[4 * H], y1 = 0.f, y2 = 0.f, y3 = 0.f;
+    int k = 0;
+    for (; k + 4 <= H; k += 4) {
+        y0 = fmaf(w2[k], fmaxf(fmaf(W1[2 * k], f0, fmaf(W1[2 * k + 1], f1, b1[k])), 0.f), y0);
+        y1 = fmaf(w2[k + 1], fmaxf(fmaf(W1[2 * k + 2], f0, fmaf(W1[2 * k + 3], f1, b1[k + 1])), 0.f), y1);
+        y2 = fmaf(w2[k + 2], fmaxf(fmaf(W1[2 * k + 4], f0, fmaf(W1[2 * k + 5], f1, b1[k + 2])), 0.f), y2);
+        y3 = fmaf(w2[k + 3], fmaxf(fmaf(W1[2 * k + 6], f0, fmaf(W1[2 * k + 7], f1, b1[k + 3])), 0.f), y3);
+    }
+    for (; k < H; ++k) y0 = fmaf(w2[k], fmaxf(fmaf(W1[2 * k], f0, fmaf(W1[2 * k + 1], f1, b1[k])), 0.f), y0);
+    return (y0 + y1) + (y2 + y3);
+}
+
+// Proposal for key q: r0 (exact rank of the segment's left knot), the float
+// offset from it, and the window half-width in base ranks (three times the
+// segment's calibrated error, the global one when the segment saw no
+// labels, plus a margin: a single fallback in a launch of ~10^5 searches
+// puts a full search on the launch's critical path, and doubling the window
+// costs one probe).
+struct Proposal { int64_t r0; float off, w; };
+
+__device__ __forceinline__ Proposal propose(const float* sK, const float* sp, const CdfView& mv, const int64_t* R,
+                                            float eps_global, float q) {
+    const int S = mv.S;
+    const int s = seg_smem(sK, S, q);
+    const float k0 = sK[s], k1 = sK[s + 1];
+    const float wk = k1 - k0;
+    float t = (wk > 0.f) ? (q - k0) / wk : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const int64_t r0 = R[s];
+    const float seg = (float)(R[s + 1] - r0);
+    const float scale = fmaxf(seg, 1.f);
+    const float y = mlp_ilp(sp, mv.H, 2.f * t - 1.f, (2.f * s + 1.f) / (float)S - 1.f);
+    float e = mv.eps_seg[s];
+    if (!(e > 0.f)) e = eps_global;
+    Proposal pr;
+    pr.r0 = r0;
+    pr.off = t * seg + y * scale;
+    pr.w = 3.f * e * scale + 32.f;
+    return pr;
+}
+
+// Window around the exact base rank r0 + off (float offset only: no loss of
+// precision for ranks beyond 2^24).
+__device__ __forceinline__ void base_window(const Proposal& pr, int64_t n, int64_t& lo, int64_t& hi) {
+    const int64_t a = pr.r0 + (int64_t)floorf(pr.off - pr.w);
+    const int64_t b = pr.r0 + (int64_t)ceilf(pr.off + pr.w);
+    lo = a < 0 ? 0 : (a > n ? n : a);
+    hi = b < 0 ? 0 : (b > n ? n : b);
     if (lo > hi) lo = hi;
 }
 
+// Steps 1-2 with the model on the searches into the base.  The A-block
+// starts search the batch B and the knot updates search B too: B is small
+// and the upper levels of those bisections are shared by all threads and
+// stay in L2, so they use the plain bisection.  The B-block starts search
+// the large base A, where every bisection would end in ~6 distinct DRAM
+// lines: there the model's window replaces the whole descent.
 __global__ void __launch_bounds__(256)
 learned_cross_rank_kernel(CdfView mv, CdfHeader* hdr, const float* __restrict__ A, int64_t n,
                           const float* __restrict__ B, int64_t m, int64_t p, int64_t* __restrict__ xbar,
                           int64_t* __restrict__ ybar, int advance) {
     extern __shared__ float sm[];
     const int P = 4 * mv.H + 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) sm[i] = mv.params[i];
-    __syncthreads();
+    float* sp = sm;                                    // MLP parameters
+    float* sK = sm + P;                                // knot keys
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double N = (double)hdr->N;
+    const int64_t cta_lo = (int64_t)blockIdx.x * blockDim.x, cta_hi = cta_lo + blockDim.x;
+    const bool model_here = cta_hi > p && cta_lo < 2 * p;   // CTA holds B-side searches
+    if (model_here) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) sp[i] = mv.params[i];
+        for (int i = threadIdx.x; i <= mv.S; i += blockDim.x) sK[i] = mv.K[i];
+    }
+    __syncthreads();
     const float eps = hdr->eps_frac;
     const int64_t* R = mv.ranks();
     int fell = 0, used = 0;
-    if (t < p) {                                       // A-side: rank_low(A[x_i], B), B a fresh batch
+    if (t < p) {                                       // A-side: rank_low(A[x_i], B)
         const int64_t xi = block_start<int64_t>(n, p, t);
-        int64_t r = m;
-        if (xi < n) {
-            const float key = __ldg(A + xi);
-            int64_t lo, hi;
-            batch_window(mv, sm, R, key, N, m, eps, lo, hi);
-            fell = !windowed_rank<false>(B, m, key, lo, hi, r);
-            used = 1;
-        }
-        xbar[t] = r;
+        xbar[t] = (xi < n) ? rank_low_global<float, int64_t>(B, m, __ldg(A + xi)) : m;
     } else if (t < 2 * p) {                            // B-side: rank_high(B[y_j], A) in the base
         const int64_t j = t - p;
         const int64_t yj = block_start<int64_t>(m, p, j);
         int64_t r = n;
         if (yj < m) {
             const float key = __ldg(B + yj);
-            const CdfPoint c = cdf_point(mv.K, R, mv.S, key);
-            const double pred = c.pla + (double)cdf_mlp(sm, mv.H, c.f0, c.f1) * c.scale;
-            const double w = base_window(mv, c, eps);
-            int64_t lo = (int64_t)fmax(0.0, floor(pred - w)), hi = (int64_t)fmin((double)n, ceil(pred + w));
-            if (lo > hi) lo = hi;
+            const Proposal pr = propose(sK, sp, mv, R, eps, key);
+            int64_t lo, hi;
+            base_window(pr, n, lo, hi);
             fell = !windowed_rank<true>(A, n, key, lo, hi, r);
             used = 1;
         }
@@ -354,15 +403,7 @@ learned_cross_rank_kernel(CdfView mv, CdfHeader* hdr, const float* __restrict__ 
         ybar[p] = n;
     } else if (advance && t <= 2 * p + 1 + mv.S) {     // knot ranks of the merged base
         const int s = (int)(t - 2 * p - 1);
-        int64_t add = m;
-        if (s < mv.S) {
-            const float key = __ldg(mv.K + s);
-            int64_t lo, hi;
-            batch_window(mv, sm, R, key, N, m, eps, lo, hi);
-            fell = !windowed_rank<false>(B, m, key, lo, hi, add);
-            used = 1;
-        }
-        mv.next_ranks()[s] = R[s] + add;
+        mv.next_ranks()[s] = R[s] + (s < mv.S ? rank_low_global<float, int64_t>(B, m, __ldg(mv.K + s)) : m);
     }
     // warp-aggregated counters
     const unsigned f = __ballot_sync(0xffffffffu, fell), u = __ballot_sync(0xffffffffu, used);
@@ -511,7 +552,9 @@ tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const fl
     const int P = 4 * hidden + 1;
     CdfView v = cdf_view(model, segments, hidden);
     const int64_t threads = 2 * p + 2 + segments;
-    learned_cross_rank_kernel<<<(unsigned)((threads + 255) / 256), 256, P * sizeof(float), s>>>(
+    const size_t smem = (size_t)(P + segments + 1) * sizeof(float);
+    if (!ensure_smem_limit(learned_cross_rank_kernel, (uint32_t)smem)) return TM_ERR_UNSUPPORTED;
+    learned_cross_rank_kernel<<<(unsigned)((threads + 255) / 256), 256, smem, s>>>(
         v, static_cast<CdfHeader*>(model), a_keys, n, b_keys, m, p, xbar, ybar, flags & TM_LEARNED_ADVANCE);
     if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
     if (flags & TM_LEARNED_ADVANCE) {

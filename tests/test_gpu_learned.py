@@ -165,8 +165,8 @@ def test_forced_fallback_still_exact():
 def test_gain_of_the_trained_network():
     """What the trained network gains over the method without it.  Plain
     Steps 1-2 bisect the whole base: log2 N probes per search.  The trained
-    model proposes each rank and leaves a window of 2 eps_s segment units
-    (eps_s its calibrated error in the key's segment): far fewer probes, every
+    model proposes each rank and leaves a window of 3 eps_s segment units
+    (eps_s its calibrated error in the key's segment, times 3): far fewer probes, every
     answer still exact.  Against its own piecewise-linear part alone (MLP
     output 0), training lowers the objective (mean squared residual); the
     per-segment maximum errors, which set the windows, are printed."""
@@ -180,8 +180,8 @@ def test_gain_of_the_trained_network():
     seg = N / 4096
     e_mlp = model.eps_segments().cpu().numpy()
     e_pla = pla.eps_segments().cpu().numpy()
-    w_mlp = np.log2(2 * (2 * e_mlp * seg + 16) + 1)
-    w_pla = np.log2(2 * (2 * e_pla * seg + 16) + 1)
+    w_mlp = np.log2(2 * (3 * e_mlp * seg + 32) + 1)
+    w_pla = np.log2(2 * (3 * e_pla * seg + 32) + 1)
     print(f"loss: pla {loss_pla.item():.3e} mlp {loss_mlp.item():.3e}; median eps_s: pla {np.median(e_pla):.4f} "
           f"mlp {np.median(e_mlp):.4f}; mean window probes: plain {np.log2(N):.1f} pla {w_pla.mean():.2f} "
           f"mlp {w_mlp.mean():.2f}")
