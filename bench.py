@@ -143,6 +143,20 @@ class ClockSampler:
                 "samples": len(load)}
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (all ranks get it)."""
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def make_inputs(device, log2n=28, dists=None, skewed_too=True):
     from paper_1202_6575_gb300 import workloads as W
     items = []
@@ -542,11 +556,8 @@ def main():
     per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][2].elapsed_time(evs[s][k][3]) for s in range(args.steps)]))
                          for k, it in enumerate(items)}
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t.item())
-    value = elems_per_step * args.steps * world / (elapsed_max / 1e3)
+    elapsed_max = max_over_ranks(elapsed_ms, dev)
+    value = whole_job_rate(elems_per_step * args.steps, world, elapsed_max)
 
     peak, peak_kind = measured_peaks()
     launches = len(items) * args.steps
@@ -600,10 +611,8 @@ def main():
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": elems_per_step * args.e2e_steps * world / (float(te.item()) / 1e3), "unit": UNIT,
+        te = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": whole_job_rate(elems_per_step * args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "pinned host -> tm_merge (C ABI) -> pinned host, one stream"}
         assert tm.tm_read_status(ws) == 0

@@ -368,7 +368,7 @@ TM_API tm_status tm_merge_learned(void* model, int segments, int hidden,
  * The cross ranks live in one file-scope device array inside the library,
  * 4 MiB, which every GPU that loads the library keeps until the process
  * exits.  It holds p + 1 <= 262144 entries per side, so (n, m, cfg) must give
- * tm_merge_blocks() <= 262143 (about 2^30 elements at the default tile);
+ * tm_merge_blocks() <= 262143 (about 2^29 elements at the default tile);
  * larger requests return TM_ERR_WORKSPACE and launch nothing.
  * The first call on each device looks the array's device address up once
  * (cudaGetSymbolAddress); make that first call before any stream capture.
