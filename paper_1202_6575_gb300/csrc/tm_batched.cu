@@ -310,50 +310,114 @@ static tm_status batched_typed(int64_t pairs, const int64_t* a_off, const void* 
 // Stable merge sort (Section 3): stable sorted runs, then merge rounds
 // ---------------------------------------------------------------------------
 
-// Stable in-CTA sort of consecutive runs of RUN elements: every element's
-// final place within its run is found with the position formulas of
-// Section 2 applied to pairs of sorted sub-runs (A-side elements at
-// i + rank_low, B-side at j + rank_high), doubling the sub-run length from 1
-// to RUN; sub-runs ping-pong between two shared-memory buffers.
-template <typename K, int RUN>
-__global__ void __launch_bounds__(RUN)
+// Stable in-CTA sort of consecutive runs of 1024 elements (Section 3's
+// "sort p consecutive blocks sequentially", done by one CTA per block):
+// 128 threads hold 9 consecutive elements each in registers and sort them
+// with an odd-even transposition network that exchanges only on a strict
+// '>' (stable); then 7 merge levels double the sorted run length from 9 to
+// 1152 >= 1024.  At each level thread t owns 9 consecutive outputs of its
+// pair of runs: it finds where its output diagonal crosses the two runs with
+// the co-rank condition of the position formulas (Section 2: i elements of
+// the left run precede output d iff R[d-i-1] < L[i] and L[i-1] <= R[d-i])
+// and merges its 9 outputs serially, taking the right run only on a
+// strictly smaller key.  Runs live in shared memory between levels; the odd
+// count per thread keeps the register <-> shared exchanges free of bank
+// conflicts (lanes 9 words apart).
+constexpr int kSortRun = 1024;
+constexpr int kSortThreads = 128;
+constexpr int kSortVT = 9;
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
 run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K* __restrict__ out_k,
                 uint32_t* __restrict__ out_v, int64_t n) {
-    __shared__ K sk[2][RUN];
-    __shared__ uint32_t sv[2][RUN];
+    __shared__ K sk[kSortRun];
+    __shared__ uint32_t sv[kSortRun];
     const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * RUN;
-    const int len = (int)(n - base < RUN ? n - base : RUN);
-    if (t < len) { sk[0][t] = in_k[base + t]; sv[0][t] = in_v[base + t]; }
+    const int64_t base = (int64_t)blockIdx.x * kSortRun;
+    const int len = (int)(n - base < kSortRun ? n - base : kSortRun);
+    for (int i = t; i < len; i += kSortThreads) { sk[i] = in_k[base + i]; sv[i] = in_v[base + i]; }
     __syncthreads();
-    int cur = 0;
-    for (int w = 1; w < len; w <<= 1) {
-        if (t < len) {
-            const int lo = t & ~(2 * w - 1);               // pair start
-            const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
-            const K key = sk[cur][t];
-            int pos;
-            if (t < mid) {                                   // A side: i + rank_low(A[i], B)
-                const K* Bp = &sk[cur][mid];
-                int r = 0, l = hi - mid;
-                while (l > 0) { int h = l >> 1; if (Bp[r + h] < key) { r += h + 1; l -= h + 1; } else l = h; }
-                pos = lo + (t - lo) + r;
-            } else {                                         // B side: j + rank_high(B[j], A)
-                const K* Ap = &sk[cur][lo];
-                int r = 0, l = mid - lo;
-                while (l > 0) { int h = l >> 1; if (!(key < Ap[r + h])) { r += h + 1; l -= h + 1; } else l = h; }
-                pos = lo + (t - mid) + r;
+    // blocked registers: thread t holds elements [8t, 8t + 8); missing ones
+    // (past len) are marked invalid and sort to the end
+    K k[kSortVT];
+    uint32_t v[kSortVT];
+    bool ok[kSortVT];
+#pragma unroll
+    for (int q = 0; q < kSortVT; ++q) {
+        const int i = t * kSortVT + q;
+        ok[q] = i < len;
+        k[q] = K();
+        v[q] = 0u;
+        if (ok[q]) { k[q] = sk[i]; v[q] = sv[i]; }
+    }
+    // stable odd-even transposition sort of 8 (invalid elements are largest)
+#pragma unroll
+    for (int r = 0; r < kSortVT; ++r) {
+#pragma unroll
+        for (int q = r & 1; q + 1 < kSortVT; q += 2) {
+            const bool swap = ok[q + 1] && (!ok[q] || k[q + 1] < k[q]);
+            if (swap) {
+                const K tk = k[q]; k[q] = k[q + 1]; k[q + 1] = tk;
+                const uint32_t tv = v[q]; v[q] = v[q + 1]; v[q + 1] = tv;
+                const bool to = ok[q]; ok[q] = ok[q + 1]; ok[q + 1] = to;
             }
-            sk[cur ^ 1][pos] = key;
-            sv[cur ^ 1][pos] = sv[cur][t];
+        }
+    }
+    for (int w = kSortVT; w < kSortRun; w <<= 1) {
+        __syncthreads();                                  // previous level's reads are done
+#pragma unroll
+        for (int q = 0; q < kSortVT; ++q) {
+            const int i = t * kSortVT + q;
+            if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
         }
         __syncthreads();
-        cur ^= 1;
+        const int d0 = t * kSortVT;                       // first output this thread owns
+        const int lo = (d0 / (2 * w)) * (2 * w);          // start of its pair of runs (w = 9 * 2^k)
+        const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
+        const int nl = mid - lo, nr = hi - mid;
+        const int d = d0 - lo;                            // diagonal inside the pair
+        int cnt = min(kSortVT, hi - d0);
+        if (cnt < 0) cnt = 0;
+        const K* L = sk + lo;
+        const K* Rr = sk + mid;
+        int i = 0, j = 0;
+        if (cnt > 0) {
+            int a = d > nr ? d - nr : 0, b = d < nl ? d : nl;
+            while (a < b) {
+                const int m2 = (a + b) >> 1;
+                if (Rr[d - m2 - 1] < L[m2]) b = m2; else a = m2 + 1;
+            }
+            i = a;
+            j = d - a;
+        }
+        K kl = (i < nl) ? L[i] : K(), kr = (j < nr) ? Rr[j] : K();
+#pragma unroll
+        for (int q = 0; q < kSortVT; ++q) {
+            ok[q] = q < cnt;
+            if (q < cnt) {
+                const bool takeR = (j < nr) && ((i >= nl) || (kr < kl));
+                if (takeR) {
+                    k[q] = kr; v[q] = sv[mid + j]; ++j;
+                    kr = (j < nr) ? Rr[j] : kr;
+                } else {
+                    k[q] = kl; v[q] = sv[lo + i]; ++i;
+                    kl = (i < nl) ? L[i] : kl;
+                }
+            }
+        }
     }
-    if (t < len) { out_k[base + t] = sk[cur][t]; out_v[base + t] = sv[cur][t]; }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSortVT; ++q) {
+        const int i = t * kSortVT + q;
+        if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
+    }
+    __syncthreads();
+    for (int i = t; i < len; i += kSortThreads) { out_k[base + i] = sk[i]; out_v[base + i] = sv[i]; }
 }
 
-constexpr int kSortRun = 1024;
+
 
 // Pair set of the merge round with sorted runs of length `run`.
 static PairSet sort_round(int64_t n, int64_t run, int64_t tile, int64_t* items) {
@@ -398,7 +462,7 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
     int src = (rounds % 2 == 0) ? 0 : 1;
     const int64_t runs = (n + kSortRun - 1) / kSortRun;
     if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
-    run_sort_kernel<K, kSortRun><<<(unsigned)runs, kSortRun, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
+    run_sort_kernel<K><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
     if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
     for (int64_t run = kSortRun; run < n; run *= 2) {
         int64_t items = 0;
