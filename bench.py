@@ -62,9 +62,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha() -> str:
+# Source files each profiled kernel is compiled from; a profile's counters
+# stand only while these files are unchanged.
+KERNEL_SOURCES = {
+    "merge_engine_kernel": ["tm_engine.cuh", "tm_engine_launch.cuh", "tm_engine_i32.cu", "tm_engine_u32.cu",
+                            "tm_engine_u64.cu", "tm_engine_f32.cu", "tm_common.cuh", "tm_host.h"],
+}
+
+
+def kernel_source_sha(kernel: str = "merge_engine_kernel") -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1202_6575_gb300", "csrc", "*"))):
+    names = KERNEL_SOURCES.get(kernel)
+    files = ([os.path.join(ROOT, "paper_1202_6575_gb300", "csrc", f) for f in names] if names else
+             sorted(glob.glob(os.path.join(ROOT, "paper_1202_6575_gb300", "csrc", "*"))))
+    for f in files:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -73,7 +84,7 @@ def kernel_source_sha() -> str:
 def profile_traffic(kernel: str):
     """DRAM bytes per output element of `kernel` from the committed ncu
     summary, if it was taken on the current kernel sources."""
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         txt = open(path).read()
         m_k = re.search(r"^kernel:\s*(\S+)", txt, re.M)
@@ -220,18 +231,25 @@ def run_reference(args, rank, world):
 
 
 def cpu_baseline(items):
-    """Times the oracle, as it stands, on one merge of each input (host copies)."""
+    """Times the oracle, as it stands, on one merge of each input (host
+    copies), and compares its results with the end-to-end run's outputs."""
     import oracle
     oracle.build()
     hosts = [(it["hA"], it["hAv"].view(np.uint32), it["hB"], it["hBv"].view(np.uint32)) for it in items]
     elems = sum(len(h[0]) + len(h[2]) for h in hosts)
-    t0 = time.perf_counter()
-    for A, Av, B, Bv in hosts:
-        oracle.merge_two_pointer(A, Av, B, Bv)
-    dt = time.perf_counter() - t0
+    same = True
+    dt = 0.0
+    for it, (A, Av, B, Bv) in zip(items, hosts):
+        t0 = time.perf_counter()
+        K, V = oracle.merge_two_pointer(A, Av, B, Bv)
+        dt += time.perf_counter() - t0
+        if "hC" in it:
+            same = same and np.array_equal(it["hC"].numpy(), K.view(np.int32)) and \
+                np.array_equal(it["hCv"].numpy().view(np.uint32), V)
     return {"value": elems / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "each of the eight merges once (the full workload, one pass), single-thread "
-                      "two-pointer merge of oracle/tm_oracle.c", "seconds": dt}
+                      "two-pointer merge of oracle/tm_oracle.c", "seconds": dt,
+            "e2e_outputs_equal_oracle": bool(same)}
 
 
 def bench_batched(dev, steps: int = 10):
@@ -571,7 +589,11 @@ def main():
                 "search_share": search_ms / (search_ms + plan_ms + merge_ms),
                 "plan_share": plan_ms / (search_ms + plan_ms + merge_ms)}
 
-    # End to end: pinned host inputs -> device, merge through tm_merge, result -> host.
+    # End to end: pinned host inputs -> device, merge through tm_merge, result
+    # -> host, for every merge of the step.  Copies in, merges and copies out
+    # run on three streams, pipelined across the eight merges (merge k's
+    # output goes to one of two device buffers, reused by merge k + 2 once
+    # its copy-out has finished).
     e2e = None
     cpu = None
     if not args.no_e2e:
@@ -579,43 +601,64 @@ def main():
         for it in items:
             it["hA"], it["hAv"], it["hB"], it["hBv"] = (pin(it["A"]).numpy(), pin(it["Av"]).numpy(),
                                                         pin(it["B"]).numpy(), pin(it["Bv"]).numpy())
-        hC = torch.empty(cmax, dtype=torch.int32, pin_memory=True)
-        hCv = torch.empty(cmax, dtype=torch.int32, pin_memory=True)
-        ws = tm.new_workspace(max(tm.tm_merge_workspace_size(it["n"], it["m"], cfg) for it in items), dev)
+            it["hC"] = torch.empty(it["n"] + it["m"], dtype=torch.int32, pin_memory=True)
+            it["hCv"] = torch.empty(it["n"] + it["m"], dtype=torch.int32, pin_memory=True)
+        Cs = [(C, Cv), (torch.empty(cmax, dtype=torch.int32, device=dev), torch.empty(cmax, dtype=torch.int32, device=dev))]
+        wss = [tm.new_workspace(max(tm.tm_merge_workspace_size(it["n"], it["m"], cfg) for it in items), dev)
+               for _ in range(2)]
+        s_in, s_comp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         h2d = d2h = 0
 
         def e2e_step():
             nonlocal h2d, d2h
             h2d = d2h = 0
-            for it in items:
+            out_done = [None, None]
+            for k, it in enumerate(items):
                 n, m = it["n"], it["m"]
-                A = it["A"]; Av = it["Av"]; B = it["B"]; Bv = it["Bv"]
-                A.copy_(torch.from_numpy(it["hA"]), non_blocking=True)
-                Av.copy_(torch.from_numpy(it["hAv"]), non_blocking=True)
-                B.copy_(torch.from_numpy(it["hB"]), non_blocking=True)
-                Bv.copy_(torch.from_numpy(it["hBv"]), non_blocking=True)
-                tm.tm_merge("i32", A, Av, B, Bv, C[:n + m], Cv[:n + m], ws, cfg=cfg, stream=stream)
-                hC[:n + m].copy_(C[:n + m], non_blocking=True)
-                hCv[:n + m].copy_(Cv[:n + m], non_blocking=True)
+                with torch.cuda.stream(s_in):
+                    it["A"].copy_(torch.from_numpy(it["hA"]), non_blocking=True)
+                    it["Av"].copy_(torch.from_numpy(it["hAv"]), non_blocking=True)
+                    it["B"].copy_(torch.from_numpy(it["hB"]), non_blocking=True)
+                    it["Bv"].copy_(torch.from_numpy(it["hBv"]), non_blocking=True)
+                    ev_in = torch.cuda.Event()
+                    ev_in.record(s_in)
+                b = k % 2
+                s_comp.wait_event(ev_in)
+                if out_done[b] is not None:
+                    s_comp.wait_event(out_done[b])
+                Cb, Cvb = Cs[b]
+                tm.tm_merge("i32", it["A"], it["Av"], it["B"], it["Bv"], Cb[:n + m], Cvb[:n + m], wss[b], cfg=cfg,
+                            stream=s_comp)
+                ev_c = torch.cuda.Event()
+                ev_c.record(s_comp)
+                s_out.wait_event(ev_c)
+                with torch.cuda.stream(s_out):
+                    it["hC"].copy_(Cb[:n + m], non_blocking=True)
+                    it["hCv"].copy_(Cvb[:n + m], non_blocking=True)
+                    out_done[b] = torch.cuda.Event()
+                    out_done[b].record(s_out)
                 h2d += 2 * (n + m) * 4
                 d2h += 2 * (n + m) * 4
 
         e2e_step()
         torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
-        e0.record(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s_in)
         for _ in range(args.e2e_steps):
             e2e_step()
-        e1.record(stream)
+            s_in.wait_stream(s_out)            # next step's copies start after this step's last copy-out
+        e1.record(s_in)
         torch.cuda.synchronize(dev)
         te = max_over_ranks(e0.elapsed_time(e1), dev)
         e2e = {"value": whole_job_rate(elems_per_step * args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-               "path": "pinned host -> tm_merge (C ABI) -> pinned host, one stream"}
-        assert tm.tm_read_status(ws) == 0
+               "path": "pinned host -> H2D (stream 1) -> tm_merge (C ABI, stream 2) -> D2H (stream 3) -> pinned "
+                       "host, pipelined over the eight merges of a step"}
+        for w in wss:
+            assert tm.tm_read_status(w, stream=s_comp) == 0
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(items)
 
