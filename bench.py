@@ -252,6 +252,39 @@ def cpu_baseline(items):
             "e2e_outputs_equal_oracle": bool(same)}
 
 
+def bench_small_merge(dev, steps: int = 200):
+    """The 1M merge: A n = 2**20, B m = 2**19 u32 keys in [0, 2**16), p = 1024
+    blocks per input; one tm_merge captured in a CUDA graph and replayed (a
+    merge of 25 MB is launch-latency bound)."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    A, Av, B, Bv = W.single_merge_1m(dev)
+    n, m = A.numel(), B.numel()
+    cfg = {"p": 1024}
+    C = torch.empty(n + m, dtype=torch.int32, device=dev)
+    Cv = torch.empty(n + m, dtype=torch.int32, device=dev)
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
+    s = torch.cuda.Stream(dev)
+    tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
+    s.synchronize()
+    with tm.Graph(s) as g:
+        tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
+    for _ in range(10):
+        g.launch()
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        g.launch()
+    e1.record(s)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    assert tm.tm_read_status(ws, stream=s) == 0
+    return {"workload": "A 2^20 + B 2^19 u32 keys in [0, 2^16), u32 payloads, p = 1024; one CUDA graph replay "
+                        "per merge (memset, search, plan, memset, tile merge)",
+            "elements": n + m, "us_per_merge": us, "value": (n + m) / (us / 1e6), "unit": UNIT,
+            "gbs": (n + m) * 16 / (us / 1e6) / 1e9}
+
+
 def bench_batched(dev, steps: int = 10):
     """Batched form: 65,536 independent pairs (lengths log-uniform in
     [1, 2**16] per side, u64 keys + u32 payloads), autotuned, captured in a
@@ -463,7 +496,7 @@ def main():
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
-    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned"],
+    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
     ap.add_argument("--log2-base", type=int, default=28, help="learned form: base size (profiling)")
@@ -484,6 +517,8 @@ def main():
             out = bench_batched(dev)
         elif args.form == "sort":
             out = bench_sort(dev)
+        elif args.form == "small":
+            out = bench_small_merge(dev)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)
@@ -669,7 +704,8 @@ def main():
         for it in items:
             it.clear()
         torch.cuda.empty_cache()
-        forms = {"batched": bench_batched(dev), "merge_sort": bench_sort(dev)}
+        forms = {"merge_1m_p1024": bench_small_merge(dev), "batched": bench_batched(dev),
+                 "merge_sort": bench_sort(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
     if rank == 0:

@@ -86,6 +86,13 @@ typedef struct tm_config {
                            (1 when two do not fit in shared memory) */
     int32_t split;      /* how a CTA divides its staged tile among its threads:
                            TM_SPLIT_DIAGONAL (2; also 0 = default) or TM_SPLIT_BLOCKS (1) */
+    int32_t wait_ms;    /* limit of every wait of the persistent tile kernel on a stage
+                           barrier, in milliseconds; default 2000.  When a wait gives up the
+                           kernel sets TM_ERR_TIMEOUT in the status word and returns. */
+    int32_t test_drop_tile; /* testing only (0 = off): each CTA of the persistent tile kernel
+                           withholds the readiness signal of its test_drop_tile-th staged
+                           tile, so its consumers' wait runs out (TM_ERR_TIMEOUT); the
+                           merge result is then incomplete.  Exercises the bounded waits. */
     int32_t reserved;
 } tm_config;
 

@@ -192,6 +192,8 @@ struct EngineArgs {
     void* C; uint32_t* Cv;
     int cap;                       // max nA + nB of any tile
     int grab;                      // records per queue grab (<= 32)
+    uint64_t wait_ns;              // limit of every mbarrier wait
+    int drop_fill;                 // testing: fill index whose readiness signal is withheld (-1: none)
     EngineLayout lay;
 };
 
@@ -316,12 +318,16 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
             const int s = k % S_IN;
             int free_ok = 1;
             if (lane == 0 && k >= S_IN)
-                free_ok = mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, kWaitLimitNs) ? 1 : 0;
+                free_ok = mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns) ? 1 : 0;
             free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
             if (!free_ok) {
                 if (lane == 0) set_status(g.status, TM_ERR_TIMEOUT);
                 ok = false;
                 break;
+            }
+            if (k == g.drop_fill) {                    // testing: this stage never becomes ready
+                ++k;
+                continue;
             }
             uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
             // piece of this lane: 0 A keys, 1 A payloads, 2 B keys, 3 B payloads
@@ -369,7 +375,7 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
     }
     if (lane == 0 && ok) {                            // end marker for the consumers
         const int s = k % S_IN;
-        if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, kWaitLimitNs)) {
+        if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns)) {
             set_status(g.status, TM_ERR_TIMEOUT);
         } else {
             StageHeader* h = reinterpret_cast<StageHeader*>(smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes);
@@ -391,7 +397,7 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
         const int s = k % S_IN;
         const int ob = k % S_OUT;
         uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
-        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, kWaitLimitNs)) {
+        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, g.wait_ns)) {
             if (leader) set_status(g.status, TM_ERR_TIMEOUT);
             break;
         }
@@ -465,7 +471,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
     for (int k = 0;; ++k) {
         const int s = k % S_IN;
         uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
-        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, kWaitLimitNs)) {
+        if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, g.wait_ns)) {
             if (leader) set_status(g.status, TM_ERR_TIMEOUT);
             break;
         }

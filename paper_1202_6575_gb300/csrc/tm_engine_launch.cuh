@@ -13,6 +13,8 @@ template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT>
 tm_status launch_engine_s(const EngineArgs& a_in, const tm_config* cfg, cudaStream_t s) {
     EngineArgs a = a_in;
     a.lay = make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, S_IN, S_OUT);
+    a.wait_ns = (cfg && cfg->wait_ms > 0) ? (uint64_t)cfg->wait_ms * 1000000ull : kWaitLimitNs;
+    a.drop_fill = (cfg && cfg->test_drop_tile > 0) ? cfg->test_drop_tile - 1 : -1;
     auto kern = merge_engine_kernel<K, LOG_T, S_IN, S_OUT, SPLIT, VT>;
     if (!ensure_smem_limit(kern, a.lay.total)) return TM_ERR_UNSUPPORTED;
     const int block = (1 << LOG_T) + 32;

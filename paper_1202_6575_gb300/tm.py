@@ -37,7 +37,7 @@ class TmConfig(ctypes.Structure):
     """struct tm_config of include/tm.h (0 = default in every field)."""
     _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
