@@ -304,7 +304,8 @@ TM_API void tm_graph_destroy(tm_graph* g);
  * Memory: one caller-owned device buffer of tm_cdf_model_bytes(S, H) bytes
  * (256-byte aligned).  Layout, little endian: a 256-byte header
  *   int32 S; int32 H; float eps; int32 cur; int64 N; uint64 fallbacks;
- *   uint64 learned_searches; int64 adam_steps; float loss; int32 pad;
+ *   uint64 learned_searches; int64 adam_steps; float loss; uint32 arrived
+ *   (a completion counter of tm_cross_ranks_learned, zero between calls);
  * then, each section starting on a 256-byte boundary: float K[S+1];
  * int64 R0[S+1]; int64 R1[S+1] (R_cur is R0 when cur = 0); float params[4H+1]
  * = W1 (H x 2, row major), b1 (H), w2 (H), b2; float adam_m[4H+1];
@@ -350,8 +351,12 @@ TM_API tm_status tm_cdf_calibrate(void* model, int segments, int hidden, const f
  * search the small batch by plain bisection.  With TM_LEARNED_ADVANCE in
  * flags the knot ranks of merge(A, B) are written to the other rank buffer
  * (R'[s] = R[s] + rank_low(K[s], B)) and made current, and N becomes n + m:
- * the model then describes the merged base.  Counts of learned searches and
- * of fallbacks accumulate in the header. */
+ * the model then describes the merged base (the launch's last CTA to finish
+ * flips the buffers, so calls on one model must not overlap on the GPU).
+ * Counts of learned searches and of fallbacks accumulate in the header.
+ * Inside the window the probes are placed from the data (the proposal, the
+ * segment's density, then interpolation between probed keys); bisection
+ * finishes.  The result never depends on where the probes fall. */
 TM_API tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const float* a_keys, int64_t n,
                                         const float* b_keys, int64_t m, int64_t p, int64_t* xbar, int64_t* ybar,
                                         int flags, tm_stream_t stream);

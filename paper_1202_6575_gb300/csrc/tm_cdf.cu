@@ -42,7 +42,7 @@ struct CdfHeader {
     unsigned long long learned;        // learned searches issued
     int64_t adam_step;
     float loss;
-    int32_t pad;
+    uint32_t arrived;                  // CTAs of a learned search that finished reading the ranks (0 between calls)
 };
 
 struct CdfLayout {
@@ -151,7 +151,7 @@ __global__ void cdf_init_kernel(CdfHeader* h, int S, int H, int64_t N, float* pa
     }
     if (threadIdx.x == 0) {
         h->S = S; h->H = H; h->eps_frac = 0.f; h->cur = 0; h->N = N;
-        h->fallbacks = 0; h->learned = 0; h->adam_step = 0; h->loss = 0.f; h->pad = 0;
+        h->fallbacks = 0; h->learned = 0; h->adam_step = 0; h->loss = 0.f; h->arrived = 0;
     }
 }
 
@@ -270,11 +270,56 @@ cdf_predict_kernel(CdfView mv, const float* __restrict__ q, int64_t count, float
 // HIGH = false) or X[r-1] <= x < X[r] (rank_high) searched in [lo, hi]; if the
 // window does not bracket it (checked against the definition, at most two
 // probes), a full binary search.  Returns true when the window sufficed.
+//
+// Inside the window the probes are placed from the data.  A bracket [a, b]
+// holds the answer whenever the window does: a probe at q reads X[q-1] and
+// either raises a to q (X[q-1] lies before x, so r >= q) or lowers b to q-1.
+// Any choice of q keeps that invariant, so the placement below affects only
+// the number of memory sectors touched, never the result:
+//   1. one probe at the model's estimate r0 + off;
+//   2. from its key, the estimate moves by (x - key) * rho (rho = base
+//      elements per key unit of the segment) and two probes bracket it at
+//      2.5 standard deviations of the count of elements in that key range
+//      (about sqrt of the move) plus 3;
+//   3. when both bracket ends have known keys, linear interpolation between
+//      them and two probes 4 elements either side;
+// then bisection of what is left (usually one 32-byte sector).
 template <bool HIGH>
-__device__ __forceinline__ bool windowed_rank(const float* __restrict__ X, int64_t len, float x, int64_t lo,
-                                              int64_t hi, int64_t& r) {
+__device__ __forceinline__ bool guided_rank(const float* __restrict__ X, int64_t len, float x, int64_t lo,
+                                            int64_t hi, int64_t r0, float off, float rho, int64_t& r) {
     auto before = [&](float v) { return HIGH ? !(x < v) : (v < x); };   // v belongs before x
-    int64_t a = lo, l = hi - lo;
+    int64_t a = lo, b = hi;
+    float ka = 0.f, kb = 0.f;                          // keys of X[a-1] and X[b] once probed
+    bool has_a = false, has_b = false;
+    auto clampq = [&](int64_t q) { return q <= a ? a + 1 : (q > b ? b : q); };
+    auto apply = [&](int64_t q, float v) {
+        if (before(v)) { if (q > a) { a = q; ka = v; has_a = true; } }
+        else if (q - 1 < b) { b = q - 1; kb = v; has_b = true; }
+    };
+    if (b > a) {                                       // 1. the model's estimate
+        const int64_t q1 = clampq(r0 + (int64_t)rintf(fminf(fmaxf(off, -2e9f), 2e9f)));
+        const float v1 = __ldg(X + q1 - 1);
+        apply(q1, v1);
+        if (b > a) {                                   // 2. local density from the segment
+            const float dr = (x - v1) * rho;
+            const float g = 2.5f * sqrtf(fabsf(dr)) + 3.f;
+            const float lo_off = fmaxf(dr - g, -2e9f), hi_off = fminf(dr + g, 2e9f);
+            const int64_t q2 = clampq(q1 + (int64_t)floorf(lo_off));
+            const int64_t q3 = clampq(q1 + (int64_t)ceilf(hi_off));
+            const float v2 = __ldg(X + q2 - 1), v3 = __ldg(X + q3 - 1);
+            apply(q2, v2);
+            apply(q3, v3);
+        }
+        if (b - a > 8 && has_a && has_b && kb > ka) {  // 3. interpolation between the bracket's keys
+            const float f = fminf(fmaxf((x - ka) / (kb - ka), 0.f), 1.f);
+            const int64_t c = a + (int64_t)(f * (float)(b - a + 1));
+            const int64_t q4 = clampq(c - 4), q5 = clampq(c + 4);
+            const float v4 = __ldg(X + q4 - 1), v5 = __ldg(X + q5 - 1);
+            apply(q4, v4);
+            apply(q5, v5);
+        }
+    }
+    int64_t l = b - a;
     while (l > 0) {
         const int64_t h = l >> 1;
         if (before(__ldg(X + a + h))) { a += h + 1; l -= h + 1; } else { l = h; }
@@ -292,29 +337,33 @@ __device__ __forceinline__ bool windowed_rank(const float* __restrict__ X, int64
 // r0 = R[s] exact and off = t * seg + y * max(seg, 1) a float offset.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int seg_smem(const float* K, int S, float q) {
+__device__ __forceinline__ int segment_of_key(const float* __restrict__ K, int S, float q) {
     int lo = 0, len = S - 1;                           // knots K[1..S-1] <= q
     const float* X = K + 1;
     while (len > 0) {
         const int half = len >> 1;
-        if (!(q < X[lo + half])) { lo += half + 1; len -= half + 1; } else { len = half; }
+        if (!(q < __ldg(X + lo + half))) { lo += half + 1; len -= half + 1; } else { len = half; }
     }
     return lo;
 }
 
-__device__ __forceinline__ float mlp_ilp(const float* p, int H, float f0, float f1) {
-    const float* W1 = p;
-    const float* b1 = p + 2 * H;
-    const float* w2 = p + 3 * H;
-    float y0 = p[4 * H], y1 = 0.f, y2 = 0.f, y3 = 0.f;
+// MLP output for features (f0, f1) from parameters staged per hidden unit
+// as {W1[k][0], W1[k][1], b1[k], w2[k]} (one 16-byte shared load per unit),
+// four independent partial sums.
+__device__ __forceinline__ float mlp_units(const float4* __restrict__ u, float b2, int H, float f0, float f1) {
+    float y0 = b2, y1 = 0.f, y2 = 0.f, y3 = 0.f;
     int k = 0;
     for (; k + 4 <= H; k += 4) {
-        y0 = fmaf(w2[k], fmaxf(fmaf(W1[2 * k], f0, fmaf(W1[2 * k + 1], f1, b1[k])), 0.f), y0);
-        y1 = fmaf(w2[k + 1], fmaxf(fmaf(W1[2 * k + 2], f0, fmaf(W1[2 * k + 3], f1, b1[k + 1])), 0.f), y1);
-        y2 = fmaf(w2[k + 2], fmaxf(fmaf(W1[2 * k + 4], f0, fmaf(W1[2 * k + 5], f1, b1[k + 2])), 0.f), y2);
-        y3 = fmaf(w2[k + 3], fmaxf(fmaf(W1[2 * k + 6], f0, fmaf(W1[2 * k + 7], f1, b1[k + 3])), 0.f), y3);
+        const float4 a = u[k], b = u[k + 1], c = u[k + 2], d = u[k + 3];
+        y0 = fmaf(a.w, fmaxf(fmaf(a.x, f0, fmaf(a.y, f1, a.z)), 0.f), y0);
+        y1 = fmaf(b.w, fmaxf(fmaf(b.x, f0, fmaf(b.y, f1, b.z)), 0.f), y1);
+        y2 = fmaf(c.w, fmaxf(fmaf(c.x, f0, fmaf(c.y, f1, c.z)), 0.f), y2);
+        y3 = fmaf(d.w, fmaxf(fmaf(d.x, f0, fmaf(d.y, f1, d.z)), 0.f), y3);
     }
-    for (; k < H; ++k) y0 = fmaf(w2[k], fmaxf(fmaf(W1[2 * k], f0, fmaf(W1[2 * k + 1], f1, b1[k])), 0.f), y0);
+    for (; k < H; ++k) {
+        const float4 a = u[k];
+        y0 = fmaf(a.w, fmaxf(fmaf(a.x, f0, fmaf(a.y, f1, a.z)), 0.f), y0);
+    }
     return (y0 + y1) + (y2 + y3);
 }
 
@@ -323,35 +372,38 @@ __device__ __forceinline__ float mlp_ilp(const float* p, int H, float f0, float 
 // segment's calibrated error, the global one when the segment saw no
 // labels, plus a margin: a single fallback in a launch of ~10^5 searches
 // puts a full search on the launch's critical path, and doubling the window
-// costs one probe).
-struct Proposal { int64_t r0; float off, w; };
+// costs one probe), and rho, the segment's base elements per key unit (the
+// local density that guides the probes inside the window).
+struct Proposal { int64_t r0; float off, w, rho; };
 
-__device__ __forceinline__ Proposal propose(const float* sK, const float* sp, const CdfView& mv, const int64_t* R,
+__device__ __forceinline__ Proposal propose(const float* __restrict__ K, const float4* __restrict__ units, float b2,
+                                            const CdfView& mv, const int64_t* R,
                                             float eps_global, float q) {
     const int S = mv.S;
-    const int s = seg_smem(sK, S, q);
-    const float k0 = sK[s], k1 = sK[s + 1];
+    const int s = segment_of_key(K, S, q);
+    const float k0 = __ldg(K + s), k1 = __ldg(K + s + 1);
     const float wk = k1 - k0;
     float t = (wk > 0.f) ? (q - k0) / wk : 0.f;
     t = fminf(fmaxf(t, 0.f), 1.f);
     const int64_t r0 = R[s];
     const float seg = (float)(R[s + 1] - r0);
     const float scale = fmaxf(seg, 1.f);
-    const float y = mlp_ilp(sp, mv.H, 2.f * t - 1.f, (2.f * s + 1.f) / (float)S - 1.f);
+    const float y = mlp_units(units, b2, mv.H, 2.f * t - 1.f, (2.f * s + 1.f) / (float)S - 1.f);
     float e = mv.eps_seg[s];
     if (!(e > 0.f)) e = eps_global;
     Proposal pr;
     pr.r0 = r0;
     pr.off = t * seg + y * scale;
     pr.w = 3.f * e * scale + 32.f;
+    pr.rho = (wk > 0.f) ? seg / wk : 0.f;
     return pr;
 }
 
 // Window around the exact base rank r0 + off (float offset only: no loss of
 // precision for ranks beyond 2^24).
 __device__ __forceinline__ void base_window(const Proposal& pr, int64_t n, int64_t& lo, int64_t& hi) {
-    const int64_t a = pr.r0 + (int64_t)floorf(pr.off - pr.w);
-    const int64_t b = pr.r0 + (int64_t)ceilf(pr.off + pr.w);
+    const int64_t a = pr.r0 + (int64_t)floorf(fminf(fmaxf(pr.off - pr.w, -4e9f), 4e9f));
+    const int64_t b = pr.r0 + (int64_t)ceilf(fminf(fmaxf(pr.off + pr.w, -4e9f), 4e9f));
     lo = a < 0 ? 0 : (a > n ? n : a);
     hi = b < 0 ? 0 : (b > n ? n : b);
     if (lo > hi) lo = hi;
@@ -361,43 +413,43 @@ __device__ __forceinline__ void base_window(const Proposal& pr, int64_t n, int64
 // starts search the batch B and the knot updates search B too: B is small
 // and the upper levels of those bisections are shared by all threads and
 // stay in L2, so they use the plain bisection.  The B-block starts search
-// the large base A, where every bisection would end in ~6 distinct DRAM
-// lines: there the model's window replaces the whole descent.
-__global__ void __launch_bounds__(256)
+// the large base A, where every bisection ends in ~8 distinct DRAM sectors:
+// there the model's window and the data-guided probes inside it replace the
+// descent (~5 sectors).  Those searches are the longest, so they take the
+// first thread indices (the first CTAs to be scheduled).  The knots are read
+// through L1 (16 KB, shared by every CTA on an SM); the MLP parameters are
+// staged in shared memory, one float4 per hidden unit.
+__global__ void __launch_bounds__(256, 8)
 learned_cross_rank_kernel(CdfView mv, CdfHeader* hdr, const float* __restrict__ A, int64_t n,
                           const float* __restrict__ B, int64_t m, int64_t p, int64_t* __restrict__ xbar,
                           int64_t* __restrict__ ybar, int advance) {
-    extern __shared__ float sm[];
-    const int P = 4 * mv.H + 1;
-    float* sp = sm;                                    // MLP parameters
-    float* sK = sm + P;                                // knot keys
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t cta_lo = (int64_t)blockIdx.x * blockDim.x, cta_hi = cta_lo + blockDim.x;
-    const bool model_here = cta_hi > p && cta_lo < 2 * p;   // CTA holds B-side searches
-    if (model_here) {
-        for (int i = threadIdx.x; i < P; i += blockDim.x) sp[i] = mv.params[i];
-        for (int i = threadIdx.x; i <= mv.S; i += blockDim.x) sK[i] = mv.K[i];
-    }
+    extern __shared__ float4 units[];                  // MLP parameters, one float4 per hidden unit
+    const int H = mv.H;
+    for (int k = threadIdx.x; k < H; k += blockDim.x)
+        units[k] = make_float4(mv.params[2 * k], mv.params[2 * k + 1], mv.params[2 * H + k], mv.params[3 * H + k]);
+    const float b2 = mv.params[4 * H];
     __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float eps = hdr->eps_frac;
     const int64_t* R = mv.ranks();
     int fell = 0, used = 0;
-    if (t < p) {                                       // A-side: rank_low(A[x_i], B)
-        const int64_t xi = block_start<int64_t>(n, p, t);
-        xbar[t] = (xi < n) ? rank_low_global<float, int64_t>(B, m, __ldg(A + xi)) : m;
-    } else if (t < 2 * p) {                            // B-side: rank_high(B[y_j], A) in the base
-        const int64_t j = t - p;
+    if (t < p) {                                       // B-side: rank_high(B[y_j], A) in the base
+        const int64_t j = t;
         const int64_t yj = block_start<int64_t>(m, p, j);
         int64_t r = n;
         if (yj < m) {
             const float key = __ldg(B + yj);
-            const Proposal pr = propose(sK, sp, mv, R, eps, key);
+            const Proposal pr = propose(mv.K, units, b2, mv, R, eps, key);
             int64_t lo, hi;
             base_window(pr, n, lo, hi);
-            fell = !windowed_rank<true>(A, n, key, lo, hi, r);
+            fell = !guided_rank<true>(A, n, key, lo, hi, pr.r0, pr.off, pr.rho, r);
             used = 1;
         }
         ybar[j] = r;
+    } else if (t < 2 * p) {                            // A-side: rank_low(A[x_i], B)
+        const int64_t i = t - p;
+        const int64_t xi = block_start<int64_t>(n, p, i);
+        xbar[i] = (xi < n) ? rank_low_global<float, int64_t>(B, m, __ldg(A + xi)) : m;
     } else if (t == 2 * p) {
         xbar[p] = m;
         ybar[p] = n;
@@ -411,12 +463,18 @@ learned_cross_rank_kernel(CdfView mv, CdfHeader* hdr, const float* __restrict__ 
         if (f) atomicAdd(&hdr->fallbacks, (unsigned long long)__popc(f));
         if (u) atomicAdd(&hdr->learned, (unsigned long long)__popc(u));
     }
-}
-
-// Makes the merged base current: flip the rank buffer and set N.
-__global__ void cdf_advance_kernel(CdfHeader* hdr, int64_t new_n) {
-    hdr->cur ^= 1;
-    hdr->N = new_n;
+    if (advance) {                                     // the last CTA to finish makes the new ranks current
+        __syncthreads();                               // this CTA's reads of the current ranks are done
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&hdr->arrived, 1u) == gridDim.x - 1) {
+                __threadfence();
+                hdr->cur ^= 1;
+                hdr->N = n + m;
+                hdr->arrived = 0;
+            }
+        }
+    }
 }
 
 }  // namespace pmerge
@@ -549,18 +607,12 @@ tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const fl
         (m > 0 && !aligned(b_keys, 4)) || !aligned(xbar, 8) || !aligned(ybar, 8))
         return TM_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int P = 4 * hidden + 1;
     CdfView v = cdf_view(model, segments, hidden);
     const int64_t threads = 2 * p + 2 + segments;
-    const size_t smem = (size_t)(P + segments + 1) * sizeof(float);
-    if (!ensure_smem_limit(learned_cross_rank_kernel, (uint32_t)smem)) return TM_ERR_UNSUPPORTED;
-    learned_cross_rank_kernel<<<(unsigned)((threads + 255) / 256), 256, smem, s>>>(
+    learned_cross_rank_kernel<<<(unsigned)((threads + 255) / 256), 256, (size_t)hidden * sizeof(float4), s>>>(
         v, static_cast<CdfHeader*>(model), a_keys, n, b_keys, m, p, xbar, ybar, flags & TM_LEARNED_ADVANCE);
     if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
-    if (flags & TM_LEARNED_ADVANCE) {
-        cdf_advance_kernel<<<1, 1, 0, s>>>(static_cast<CdfHeader*>(model), n + m);
-        if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
-    }
+
     return TM_OK;
 }
 

@@ -23,13 +23,13 @@ __global__ void __launch_bounds__(256)
 cross_rank_kernel(const K* __restrict__ A, int64_t n, const K* __restrict__ B, int64_t m,
                   int64_t p, int64_t* __restrict__ xbar, int64_t* __restrict__ ybar) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < p) {
-        int64_t xi = block_start<int64_t>(n, p, t);
-        xbar[t] = (xi < n) ? rank_low_global<K, int64_t>(B, m, __ldg(A + xi)) : m;
+    if (t < p) {                        // B-block starts first: with m <= n theirs are the longer searches
+        int64_t yj = block_start<int64_t>(m, p, t);
+        ybar[t] = (yj < m) ? rank_high_global<K, int64_t>(A, n, __ldg(B + yj)) : n;
     } else if (t < 2 * p) {
-        int64_t j = t - p;
-        int64_t yj = block_start<int64_t>(m, p, j);
-        ybar[j] = (yj < m) ? rank_high_global<K, int64_t>(A, n, __ldg(B + yj)) : n;
+        int64_t i = t - p;
+        int64_t xi = block_start<int64_t>(n, p, i);
+        xbar[i] = (xi < n) ? rank_low_global<K, int64_t>(B, m, __ldg(A + xi)) : m;
     } else if (t == 2 * p) {
         xbar[p] = m;
         ybar[p] = n;
