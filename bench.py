@@ -626,9 +626,10 @@ def main():
 
     # End to end: pinned host inputs -> device, merge through tm_merge, result
     # -> host, for every merge of the step.  Copies in, merges and copies out
-    # run on three streams, pipelined across the eight merges (merge k's
-    # output goes to one of two device buffers, reused by merge k + 2 once
-    # its copy-out has finished).
+    # run on three streams, pipelined across the eight merges and across
+    # steps (merge k's output goes to one of two device buffers, reused by
+    # merge k + 2 once its copy-out has finished; a step's copy into merge
+    # k's inputs waits for the previous step's merge k).
     e2e = None
     cpu = None
     if not args.no_e2e:
@@ -643,13 +644,16 @@ def main():
                for _ in range(2)]
         s_in, s_comp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         h2d = d2h = 0
+        out_done = [None, None]
+        merged = {}                       # per merge: its last tm_merge, which read the device inputs
 
         def e2e_step():
             nonlocal h2d, d2h
             h2d = d2h = 0
-            out_done = [None, None]
             for k, it in enumerate(items):
                 n, m = it["n"], it["m"]
+                if k in merged:               # the previous step's merge k has read these inputs
+                    s_in.wait_event(merged[k])
                 with torch.cuda.stream(s_in):
                     it["A"].copy_(torch.from_numpy(it["hA"]), non_blocking=True)
                     it["Av"].copy_(torch.from_numpy(it["hAv"]), non_blocking=True)
@@ -666,6 +670,7 @@ def main():
                             stream=s_comp)
                 ev_c = torch.cuda.Event()
                 ev_c.record(s_comp)
+                merged[k] = ev_c
                 s_out.wait_event(ev_c)
                 with torch.cuda.stream(s_out):
                     it["hC"].copy_(Cb[:n + m], non_blocking=True)
@@ -683,15 +688,15 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s_in)
         for _ in range(args.e2e_steps):
-            e2e_step()
-            s_in.wait_stream(s_out)            # next step's copies start after this step's last copy-out
+            e2e_step()                         # copies in of the next step overlap this step's copies out
+        s_in.wait_stream(s_out)
         e1.record(s_in)
         torch.cuda.synchronize(dev)
         te = max_over_ranks(e0.elapsed_time(e1), dev)
         e2e = {"value": whole_job_rate(elems_per_step * args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "pinned host -> H2D (stream 1) -> tm_merge (C ABI, stream 2) -> D2H (stream 3) -> pinned "
-                       "host, pipelined over the eight merges of a step"}
+                       "host, pipelined over the eight merges of a step and across steps"}
         for w in wss:
             assert tm.tm_read_status(w, stream=s_comp) == 0
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
