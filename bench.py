@@ -285,13 +285,13 @@ def bench_small_merge(dev, steps: int = 200):
             "gbs": (n + m) * 16 / (us / 1e6) / 1e9}
 
 
-def bench_batched(dev, steps: int = 10):
+def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = True, cfg=None):
     """Batched form: 65,536 independent pairs (lengths log-uniform in
     [1, 2**16] per side, u64 keys + u32 payloads), autotuned, captured in a
     CUDA graph, replayed `steps` times.  Compared with the plain form: the
     same pairs as 65,536 tm_merge calls on one stream."""
     from paper_1202_6575_gb300 import tm, workloads as W
-    a_off, A, Av, b_off, B, Bv = W.batched_pairs(dev)
+    a_off, A, Av, b_off, B, Bv = W.batched_pairs(dev, pairs=pairs)
     pairs = a_off.numel() - 1
     ta, tb = A.numel(), B.numel()
     total = ta + tb
@@ -300,7 +300,7 @@ def bench_batched(dev, steps: int = 10):
     big = max(tm.tm_merge_batched_workspace_size(pairs, ta, tb, {"tile": t}) for t in (1024, 2048, 4096))
     ws = tm.new_workspace(big, dev)
     s = torch.cuda.Stream(dev)
-    best = tm.tm_autotune_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, stream=s)
+    best = cfg or tm.tm_autotune_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, stream=s)
     tm.tm_merge_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, cfg=best, stream=s)
     s.synchronize()
     with tm.Graph(s) as g:
@@ -316,30 +316,33 @@ def bench_batched(dev, steps: int = 10):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     assert tm.tm_read_status(ws, stream=s) == 0
-    # plain form: one tm_merge per pair (host loop, one stream)
-    ho_a, ho_b = a_off.cpu().tolist(), b_off.cpu().tolist()
-    wsp = tm.new_workspace(tm.tm_merge_workspace_size(1 << 16, 1 << 16), dev)
-    def plain():
-        for k in range(pairs):
-            a0, a1, b0, b1 = ho_a[k], ho_a[k + 1], ho_b[k], ho_b[k + 1]
-            c0 = a0 + b0
-            L = (a1 - a0) + (b1 - b0)
-            tm.tm_merge("u64", A[a0:a1], Av[a0:a1], B[b0:b1], Bv[b0:b1], C[c0:c0 + L], Cv[c0:c0 + L], wsp, stream=s)
-    plain()
-    s.synchronize()
-    e0.record(s)
-    plain()
-    e1.record(s)
-    e1.synchronize()
-    ms_plain = e0.elapsed_time(e1)
+    ms_plain = None
+    if with_plain:
+        # plain form: one tm_merge per pair (host loop, one stream)
+        ho_a, ho_b = a_off.cpu().tolist(), b_off.cpu().tolist()
+        wsp = tm.new_workspace(tm.tm_merge_workspace_size(1 << 16, 1 << 16), dev)
+        def plain():
+            for k in range(pairs):
+                a0, a1, b0, b1 = ho_a[k], ho_a[k + 1], ho_b[k], ho_b[k + 1]
+                c0 = a0 + b0
+                L = (a1 - a0) + (b1 - b0)
+                tm.tm_merge("u64", A[a0:a1], Av[a0:a1], B[b0:b1], Bv[b0:b1], C[c0:c0 + L], Cv[c0:c0 + L], wsp, stream=s)
+        plain()
+        s.synchronize()
+        e0.record(s)
+        plain()
+        e1.record(s)
+        e1.synchronize()
+        ms_plain = e0.elapsed_time(e1)
     gbs = total * 24 / (ms / 1e3) / 1e9
-    return {"workload": "65,536 pairs, lengths log-uniform in [1, 2^16] per side, u64 keys in [0, 2^20) + u32 "
-                        "payloads; autotuned; one CUDA graph (count, scan, search, plan, persistent merge)",
+    return {"workload": f"{pairs:,} pairs, lengths log-uniform in [1, 2^16] per side, u64 keys in [0, 2^20) + u32 "
+                        f"payloads; {'fixed configuration' if cfg else 'autotuned'}; one CUDA graph (count, scan, "
+                        "search, plan, persistent merge)",
             "elements": total, "value": total / (ms / 1e3), "unit": UNIT, "ms": ms, "steps": steps,
             "config": best, "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0],
-            "plain_per_pair_tm_merge": {"value": total / (ms_plain / 1e3), "ms": ms_plain,
-                                        "calls": pairs},
-            "speedup_vs_plain": ms_plain / ms}
+            "plain_per_pair_tm_merge": None if ms_plain is None else {"value": total / (ms_plain / 1e3),
+                                                                       "ms": ms_plain, "calls": pairs},
+            "speedup_vs_plain": None if ms_plain is None else ms_plain / ms}
 
 
 def bench_sort(dev, steps: int = 3):
@@ -479,6 +482,50 @@ def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int =
             "bit_identical": bool(same)}
 
 
+def bench_search(dev, log2_base: int = 28, log2_batch: int = 20, reps: int = 30):
+    """Steps 1-2 alone on the LSM inputs: one sorted float32 base (3
+    lognormals) and one batch; the plain searches (tm_cross_ranks) vs the
+    learned ones (tm_cross_ranks_learned, model trained as in the learned
+    form), each launch after a 512 MB write that flushes L2; median of the
+    launches after 3 warm-up ones (CUDA events)."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    n, m = 1 << log2_base, 1 << log2_batch
+    A, _ = W.lsm_base(dev, n=n)
+    B, _ = W.lsm_batch(0, dev, size=m, base_n=n)
+    q = W.lsm_label_keys(dev, count=1 << 18)
+    init = W.cdf_init(hidden=64)
+    flat = torch.cat([init["W1"].reshape(-1), init["b1"], init["w2"], init["b2"].reshape(1)])
+    model = tm.CdfModel(4096, 64, dev).init(A, flat)
+    model.train(q, tm.tm_rank_search("f32", "high", q, A), steps=400, lr=3e-3)
+    qc = W.lsm_label_keys(dev, count=1 << 20, seed=W.SEED_BASE + 8)
+    model.calibrate(qc, tm.tm_rank_search("f32", "high", qc, A))
+    p = tm.tm_merge_blocks(n, m)
+    xbar = torch.empty(p + 1, dtype=torch.int64, device=dev)
+    ybar = torch.empty_like(xbar)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        ts = []
+        for r in range(reps):
+            flush.fill_(r & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts[3:]))
+
+    plain_us = timed(lambda: tm.tm_cross_ranks("f32", A, B, p, xbar, ybar, stream=s))
+    xp, yp = xbar.clone(), ybar.clone()
+    learned_us = timed(lambda: tm.tm_cross_ranks_learned(model, A, B, p, xbar, ybar, stream=s))
+    return {"workload": f"base 2^{log2_base} f32 (3 lognormals), batch 2^{log2_batch}, p = {p}",
+            "plain_us": plain_us, "learned_us": learned_us, "speedup": plain_us / learned_us,
+            "identical": bool(torch.equal(xp, xbar) and torch.equal(yp, ybar)),
+            "fallbacks": int(model.header()["fallbacks"])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,9 +543,10 @@ def main():
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
-    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small"],
+    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
+    ap.add_argument("--pairs", type=int, default=65536, help="batched form: pairs (profiling)")
     ap.add_argument("--log2-base", type=int, default=28, help="learned form: base size (profiling)")
     args = ap.parse_args()
     args.dists = [d for d in args.dists.split(",") if d] or None
@@ -514,11 +562,15 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         if args.form == "batched":
-            out = bench_batched(dev)
+            fixed = {k: v for k, v in (("tile", args.tile), ("threads", args.threads), ("stages", args.stages),
+                                       ("split", args.split)) if v} or None
+            out = bench_batched(dev, pairs=args.pairs, with_plain=args.pairs == 65536 and fixed is None, cfg=fixed)
         elif args.form == "sort":
             out = bench_sort(dev)
         elif args.form == "small":
             out = bench_small_merge(dev)
+        elif args.form == "search":
+            out = bench_search(dev, log2_base=args.log2_base)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)

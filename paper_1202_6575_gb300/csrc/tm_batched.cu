@@ -72,51 +72,104 @@ struct PairBases {
 // CSR mode: per-pair counts and their exclusive scans
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256)
-pair_count_kernel(PairSet ps, int64_t tile, int64_t* __restrict__ cnt_search, int64_t* __restrict__ cnt_rank,
-                  int64_t* __restrict__ cnt_item) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ps.num_pairs) return;
-    int64_t a0, n, b0, m, c0;
-    ps.get(k, a0, n, b0, m, c0);
-    const int64_t p = pair_blocks(n, m, tile);
-    cnt_search[k] = 2 * p;
-    cnt_rank[k] = p + 1;
-    cnt_item[k] = pair_items(n, m, p);
+// Exclusive scan of three int64 values over a CTA of NT threads (NT a
+// multiple of 32, at most 1024): warp shuffles, then the warp totals.
+template <int NT>
+__device__ __forceinline__ void block_scan3(const int64_t v[3], int64_t ex[3], int64_t tot[3]) {
+    __shared__ int64_t wsum[3][NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t in[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, in[c], off);
+            if (lane >= off) in[c] += y;
+        }
+    }
+    if (lane == 31) { wsum[0][warp] = in[0]; wsum[1][warp] = in[1]; wsum[2][warp] = in[2]; }
+    __syncthreads();
+    if (warp == 0) {                                   // scan of the warp totals
+        int64_t w[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[c] = lane < NT / 32 ? wsum[c][lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w[c], off);
+                if (lane >= off) w[c] += y;
+            }
+        }
+        if (lane < NT / 32) { wsum[0][lane] = w[0]; wsum[1][lane] = w[1]; wsum[2][lane] = w[2]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ex[c] = in[c] - v[c] + (warp ? wsum[c][warp - 1] : 0);
+        tot[c] = wsum[c][NT / 32 - 1];
+    }
+    __syncthreads();                                   // wsum may be reused by the caller's next scan
 }
 
-// Exclusive scans of three count arrays in place (one CTA of 1024 threads,
-// each scanning a contiguous chunk).  base[num] receives the totals; the
-// record total also goes to *n_items.
+// Per-pair counts (2 p_k searches, p_k + 1 cross-rank slots, records),
+// scanned within the CTA: each pair gets its exclusive prefix within its
+// CTA and part[c][blockIdx] the CTA's totals.
+__global__ void __launch_bounds__(256)
+pair_count_kernel(PairSet ps, int64_t tile, int64_t* __restrict__ cnt_search, int64_t* __restrict__ cnt_rank,
+                  int64_t* __restrict__ cnt_item, int64_t* __restrict__ part, int64_t nparts) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t v[3] = {0, 0, 0};
+    if (k < ps.num_pairs) {
+        int64_t a0, n, b0, m, c0;
+        ps.get(k, a0, n, b0, m, c0);
+        const int64_t p = pair_blocks(n, m, tile);
+        v[0] = 2 * p; v[1] = p + 1; v[2] = pair_items(n, m, p);
+    }
+    int64_t ex[3], tot[3];
+    block_scan3<256>(v, ex, tot);
+    if (k < ps.num_pairs) { cnt_search[k] = ex[0]; cnt_rank[k] = ex[1]; cnt_item[k] = ex[2]; }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot[0]; part[nparts + blockIdx.x] = tot[1]; part[2 * nparts + blockIdx.x] = tot[2];
+    }
+}
+
+// Exclusive scan of the CTA totals in place (one CTA, rounds of 1024 with a
+// running carry); the grand totals go to base[num] of the three arrays and
+// the record total to *n_items.
 __global__ void __launch_bounds__(1024)
-scan3_kernel(int64_t num, int64_t* __restrict__ s0, int64_t* __restrict__ s1, int64_t* __restrict__ s2,
-             int64_t* __restrict__ n_items) {
-    __shared__ int64_t part[3][1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = (num + 1023) / 1024;
-    const int64_t lo = t * chunk < num ? t * chunk : num;
-    const int64_t hi = lo + chunk < num ? lo + chunk : num;
-    int64_t a = 0, b = 0, c = 0;
-    for (int64_t i = lo; i < hi; ++i) { a += s0[i]; b += s1[i]; c += s2[i]; }
-    part[0][t] = a; part[1][t] = b; part[2][t] = c;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {       // inclusive Hillis-Steele scan of the partials
-        int64_t x0 = 0, x1 = 0, x2 = 0;
-        if (t >= off) { x0 = part[0][t - off]; x1 = part[1][t - off]; x2 = part[2][t - off]; }
-        __syncthreads();
-        part[0][t] += x0; part[1][t] += x1; part[2][t] += x2;
-        __syncthreads();
+part_scan_kernel(int64_t* __restrict__ part, int64_t nparts, int64_t num, int64_t* __restrict__ s0,
+                 int64_t* __restrict__ s1, int64_t* __restrict__ s2, int64_t* __restrict__ n_items) {
+    int64_t carry[3] = {0, 0, 0};
+    for (int64_t r = 0; r < nparts; r += 1024) {
+        const int64_t i = r + threadIdx.x;
+        int64_t v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = i < nparts ? part[c * nparts + i] : 0;
+        int64_t ex[3], tot[3];
+        block_scan3<1024>(v, ex, tot);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (i < nparts) part[c * nparts + i] = carry[c] + ex[c];
+            carry[c] += tot[c];
+        }
     }
-    int64_t r0 = t ? part[0][t - 1] : 0, r1 = t ? part[1][t - 1] : 0, r2 = t ? part[2][t - 1] : 0;
-    for (int64_t i = lo; i < hi; ++i) {
-        const int64_t v0 = s0[i], v1 = s1[i], v2 = s2[i];
-        s0[i] = r0; s1[i] = r1; s2[i] = r2;
-        r0 += v0; r1 += v1; r2 += v2;
+    if (threadIdx.x == 0) {
+        s0[num] = carry[0]; s1[num] = carry[1]; s2[num] = carry[2];
+        *n_items = carry[2];
     }
-    if (t == 1023) {
-        s0[num] = part[0][1023]; s1[num] = part[1][1023]; s2[num] = part[2][1023];
-        *n_items = part[2][1023];
-    }
+}
+
+// Adds each CTA's offset to its pairs' prefixes: the three arrays become
+// global exclusive prefixes.
+__global__ void __launch_bounds__(256)
+part_add_kernel(int64_t num, const int64_t* __restrict__ part, int64_t nparts, int64_t* __restrict__ s0,
+                int64_t* __restrict__ s1, int64_t* __restrict__ s2) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= num) return;
+    s0[k] += part[blockIdx.x];
+    s1[k] += part[nparts + blockIdx.x];
+    s2[k] += part[2 * nparts + blockIdx.x];
 }
 
 // Pair owning global search index t: the last k with search_base[k] <= t.
@@ -146,6 +199,53 @@ __device__ __forceinline__ bool locate(const PairSet& ps, const PairBases& pb, i
     return true;
 }
 
+// The pairs that own one CTA's search (or plan) threads: [kf, kl] from two
+// binary searches (threads 0 and 32), and their search bases staged in
+// shared memory when the range is short, so that every thread finds its pair
+// there instead of bisecting the whole prefix array in global memory.
+constexpr int kPairWin = 512;
+struct PairWin { int64_t kf; int cnt; };           // cnt staged bases (kl - kf + 2); 0: not staged
+
+__device__ __forceinline__ PairWin stage_pair_window(const PairSet& ps, const PairBases& pb, int64_t total_threads,
+                                                     int64_t* sb) {
+    __shared__ int64_t s_k[2];
+    PairWin w{0, 0};
+    if (!ps.a_off) return w;                           // uniform pairs: closed form, the same for every CTA
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t all = __ldg(pb.search_base + ps.num_pairs);
+    const int64_t tot = all < total_threads ? all : total_threads;
+    const int64_t tl = (t0 + (int64_t)blockDim.x < tot ? t0 + (int64_t)blockDim.x : tot) - 1;
+    if (threadIdx.x == 0) s_k[0] = t0 < tot ? pair_of(pb.search_base, ps.num_pairs, t0) : 0;
+    if (threadIdx.x == 32) s_k[1] = t0 < tot ? pair_of(pb.search_base, ps.num_pairs, tl) : -1;
+    __syncthreads();
+    const int64_t kf = s_k[0], cnt = s_k[1] - kf + 2;
+    if (cnt >= 2 && cnt <= kPairWin) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) sb[i] = __ldg(pb.search_base + kf + i);
+        w.kf = kf;
+        w.cnt = (int)cnt;
+    }
+    __syncthreads();
+    return w;
+}
+
+// locate() through the staged window when there is one.
+__device__ __forceinline__ bool locate_in(const PairSet& ps, const PairBases& pb, const PairWin& w,
+                                          const int64_t* sb, int64_t t, int64_t& k, int64_t& local, int64_t& p) {
+    if (ps.a_off && w.cnt) {
+        if (t >= sb[w.cnt - 1]) return false;          // past the last pair's searches
+        int lo = 0, len = w.cnt - 1;                    // last i <= cnt-2 with sb[i] <= t
+        while (len > 0) {
+            const int half = len >> 1;
+            if (sb[lo + half + 1] <= t) { lo += half + 1; len -= half + 1; } else { len = half; }
+        }
+        k = w.kf + lo;
+        local = t - sb[lo];
+        p = (sb[lo + 1] - sb[lo]) / 2;
+        return true;
+    }
+    return locate(ps, pb, t, k, local, p);
+}
+
 __device__ __forceinline__ int64_t rank_base_of(const PairSet& ps, const PairBases& pb, int64_t k) {
     return ps.a_off ? __ldg(pb.rank_base + k) : k * (ps.p_uniform + 1);
 }
@@ -159,10 +259,12 @@ template <typename K>
 __global__ void __launch_bounds__(256)
 batched_search_kernel(PairSet ps, PairBases pb, const K* __restrict__ A, const K* __restrict__ B,
                       int64_t total_threads, int64_t* __restrict__ xbar, int64_t* __restrict__ ybar) {
+    __shared__ int64_t sb[kPairWin];
+    const PairWin w = stage_pair_window(ps, pb, total_threads, sb);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total_threads) return;
     int64_t k, local, p;
-    if (!locate(ps, pb, t, k, local, p)) return;
+    if (!locate_in(ps, pb, w, sb, t, k, local, p)) return;
     int64_t a0, n, b0, m, c0;
     ps.get(k, a0, n, b0, m, c0);
     const int64_t rb = rank_base_of(ps, pb, k);
@@ -182,10 +284,12 @@ batched_search_kernel(PairSet ps, PairBases pb, const K* __restrict__ A, const K
 __global__ void __launch_bounds__(256)
 batched_plan_kernel(PairSet ps, PairBases pb, int64_t total_threads, const int64_t* __restrict__ xbar,
                     const int64_t* __restrict__ ybar, TileDesc* __restrict__ desc) {
+    __shared__ int64_t sb[kPairWin];
+    const PairWin w = stage_pair_window(ps, pb, total_threads, sb);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total_threads) return;
     int64_t k, local, p;
-    if (!locate(ps, pb, t, k, local, p)) return;
+    if (!locate_in(ps, pb, w, sb, t, k, local, p)) return;
     int64_t a0g, n, b0g, m, c0g;
     ps.get(k, a0g, n, b0g, m, c0g);
     const bool a_side = local < p;
@@ -216,6 +320,7 @@ struct BatchedWs {
     void* control;
     int64_t* n_items;                              // device record count
     int64_t *search_base, *rank_base, *item_base;  // num_pairs + 1 each (CSR)
+    int64_t* part;                                 // 3 x ceil(num_pairs / 256) CTA totals of the scan
     int64_t *xbar, *ybar;
     TileDesc* tiles;
     size_t bytes;
@@ -227,7 +332,8 @@ static int64_t tile_of(const tm_config* cfg) { return (cfg && cfg->tile > 0) ? c
 static int64_t blocks_bound(int64_t pairs, int64_t total, int64_t tile) { return total / tile + pairs; }
 
 // Workspace: control block, device record count, three per-pair prefix
-// arrays, cross ranks (ranks_cap entries per side) and tile records.
+// arrays, the scan's CTA totals, cross ranks (ranks_cap entries per side)
+// and tile records.
 static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap) {
     BatchedWs w{};
     uint8_t* b = static_cast<uint8_t*>(base);
@@ -237,6 +343,7 @@ static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t
     w.search_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
     w.rank_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
     w.item_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
+    w.part = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)3 * ((pairs + 255) / 256) * 8, 256);
     w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)items_cap * sizeof(TileDesc), 256);
@@ -261,8 +368,12 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
     int64_t threads;                               // upper bound of sum 2 p_k
     if (ps.a_off) {
         const int64_t blocks = (ps.num_pairs + 255) / 256;
-        pair_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps, tile, w.search_base, w.rank_base, w.item_base);
-        scan3_kernel<<<1, 1024, 0, s>>>(ps.num_pairs, w.search_base, w.rank_base, w.item_base, w.n_items);
+        pair_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps, tile, w.search_base, w.rank_base, w.item_base,
+                                                          w.part, blocks);
+        part_scan_kernel<<<1, 1024, 0, s>>>(w.part, blocks, ps.num_pairs, w.search_base, w.rank_base,
+                                            w.item_base, w.n_items);
+        part_add_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps.num_pairs, w.part, blocks, w.search_base,
+                                                         w.rank_base, w.item_base);
         threads = 2 * blocks_bound(ps.num_pairs, total, tile);
     } else {
         threads = 2 * ps.p_uniform * ps.num_pairs;
