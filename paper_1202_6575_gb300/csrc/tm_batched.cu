@@ -66,6 +66,7 @@ struct PairBases {
     const int64_t* search_base;    // 2 p_k prefix      (CSR)
     const int64_t* rank_base;      // (p_k + 1) prefix  (CSR)
     const int64_t* item_base;      // items prefix      (CSR)
+    const int64_t* cta_pair;       // pair of each search/plan CTA's first thread (CSR)
 };
 
 // ---------------------------------------------------------------------------
@@ -160,16 +161,24 @@ part_scan_kernel(int64_t* __restrict__ part, int64_t nparts, int64_t num, int64_
     }
 }
 
-// Adds each CTA's offset to its pairs' prefixes: the three arrays become
-// global exclusive prefixes.
+// Adds each CTA's offset to its pairs' prefixes (the three arrays become
+// global exclusive prefixes) and records, for every 256-thread CTA of the
+// search and plan kernels whose first thread falls in pair k's searches,
+// cta_pair[CTA] = k.
 __global__ void __launch_bounds__(256)
-part_add_kernel(int64_t num, const int64_t* __restrict__ part, int64_t nparts, int64_t* __restrict__ s0,
-                int64_t* __restrict__ s1, int64_t* __restrict__ s2) {
+part_add_kernel(PairSet ps, int64_t tile, const int64_t* __restrict__ part, int64_t nparts,
+                int64_t* __restrict__ s0, int64_t* __restrict__ s1, int64_t* __restrict__ s2,
+                int64_t* __restrict__ cta_pair) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= num) return;
-    s0[k] += part[blockIdx.x];
+    if (k >= ps.num_pairs) return;
+    const int64_t sk = s0[k] + part[blockIdx.x];
+    s0[k] = sk;
     s1[k] += part[nparts + blockIdx.x];
     s2[k] += part[2 * nparts + blockIdx.x];
+    int64_t a0, n, b0, m, c0;
+    ps.get(k, a0, n, b0, m, c0);
+    const int64_t ek = sk + 2 * pair_blocks(n, m, tile);
+    for (int64_t c = (sk + 255) / 256; c * 256 < ek; ++c) cta_pair[c] = k;
 }
 
 // Pair owning global search index t: the last k with search_base[k] <= t.
@@ -199,27 +208,26 @@ __device__ __forceinline__ bool locate(const PairSet& ps, const PairBases& pb, i
     return true;
 }
 
-// The pairs that own one CTA's search (or plan) threads: [kf, kl] from two
-// binary searches (threads 0 and 32), and their search bases staged in
-// shared memory when the range is short, so that every thread finds its pair
-// there instead of bisecting the whole prefix array in global memory.
+// The pairs that own one CTA's search (or plan) threads: from the first pair
+// of this CTA to the first pair of the next one (cta_pair, written with the
+// scan), their search bases staged in shared memory when the range is
+// short, so that every thread finds its pair there instead of bisecting the
+// whole prefix array in global memory.
 constexpr int kPairWin = 512;
-struct PairWin { int64_t kf; int cnt; };           // cnt staged bases (kl - kf + 2); 0: not staged
+struct PairWin { int64_t kf; int cnt; };           // cnt staged bases; 0: not staged
 
 __device__ __forceinline__ PairWin stage_pair_window(const PairSet& ps, const PairBases& pb, int64_t total_threads,
                                                      int64_t* sb) {
-    __shared__ int64_t s_k[2];
     PairWin w{0, 0};
     if (!ps.a_off) return w;                           // uniform pairs: closed form, the same for every CTA
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
     const int64_t all = __ldg(pb.search_base + ps.num_pairs);
     const int64_t tot = all < total_threads ? all : total_threads;
-    const int64_t tl = (t0 + (int64_t)blockDim.x < tot ? t0 + (int64_t)blockDim.x : tot) - 1;
-    if (threadIdx.x == 0) s_k[0] = t0 < tot ? pair_of(pb.search_base, ps.num_pairs, t0) : 0;
-    if (threadIdx.x == 32) s_k[1] = t0 < tot ? pair_of(pb.search_base, ps.num_pairs, tl) : -1;
-    __syncthreads();
-    const int64_t kf = s_k[0], cnt = s_k[1] - kf + 2;
-    if (cnt >= 2 && cnt <= kPairWin) {
+    if (t0 >= tot) return w;                           // uniform over the CTA: no thread of it has work
+    const int64_t kf = __ldg(pb.cta_pair + blockIdx.x);
+    const int64_t kl = t0 + (int64_t)blockDim.x < tot ? __ldg(pb.cta_pair + blockIdx.x + 1) : ps.num_pairs - 1;
+    const int64_t cnt = kl - kf + 2;                   // bases of pairs kf..kl and the end of kl
+    if (cnt <= kPairWin) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) sb[i] = __ldg(pb.search_base + kf + i);
         w.kf = kf;
         w.cnt = (int)cnt;
@@ -321,6 +329,7 @@ struct BatchedWs {
     int64_t* n_items;                              // device record count
     int64_t *search_base, *rank_base, *item_base;  // num_pairs + 1 each (CSR)
     int64_t* part;                                 // 3 x ceil(num_pairs / 256) CTA totals of the scan
+    int64_t* cta_pair;                             // pair of each search/plan CTA's first thread (CSR)
     int64_t *xbar, *ybar;
     TileDesc* tiles;
     size_t bytes;
@@ -332,9 +341,9 @@ static int64_t tile_of(const tm_config* cfg) { return (cfg && cfg->tile > 0) ? c
 static int64_t blocks_bound(int64_t pairs, int64_t total, int64_t tile) { return total / tile + pairs; }
 
 // Workspace: control block, device record count, three per-pair prefix
-// arrays, the scan's CTA totals, cross ranks (ranks_cap entries per side)
-// and tile records.
-static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap) {
+// arrays, the scan's CTA totals, the first pair of every search/plan CTA,
+// cross ranks (ranks_cap entries per side) and tile records.
+static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap, int64_t ctas_cap) {
     BatchedWs w{};
     uint8_t* b = static_cast<uint8_t*>(base);
     size_t o = 0;
@@ -344,6 +353,7 @@ static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t
     w.rank_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
     w.item_base = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(pairs + 1) * 8, 256);
     w.part = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)3 * ((pairs + 255) / 256) * 8, 256);
+    w.cta_pair = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(ctas_cap + 1) * 8, 256);
     w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)items_cap * sizeof(TileDesc), 256);
@@ -354,7 +364,7 @@ static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t
 // CSR pairs: sum (p_k + 1) <= P + pairs and sum items <= 2 P.
 static BatchedWs batched_ws_layout(void* base, int64_t pairs, int64_t total, int64_t tile) {
     const int64_t P = blocks_bound(pairs, total, tile);
-    return ws_layout(base, pairs, P + pairs, 2 * P);
+    return ws_layout(base, pairs, P + pairs, 2 * P, (2 * P + 255) / 256);
 }
 
 // Runs search, plan and the engine for a pair set; `ws` laid out as above.
@@ -364,7 +374,7 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
                            K* C, uint32_t* Cv, int64_t tile, int64_t known_items,
                            const tm_config* cfg, cudaStream_t s) {
     const int64_t total = total_a + total_b;
-    PairBases pb{w.search_base, w.rank_base, w.item_base};
+    PairBases pb{w.search_base, w.rank_base, w.item_base, w.cta_pair};
     int64_t threads;                               // upper bound of sum 2 p_k
     if (ps.a_off) {
         const int64_t blocks = (ps.num_pairs + 255) / 256;
@@ -372,8 +382,8 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
                                                           w.part, blocks);
         part_scan_kernel<<<1, 1024, 0, s>>>(w.part, blocks, ps.num_pairs, w.search_base, w.rank_base,
                                             w.item_base, w.n_items);
-        part_add_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps.num_pairs, w.part, blocks, w.search_base,
-                                                         w.rank_base, w.item_base);
+        part_add_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps, tile, w.part, blocks, w.search_base, w.rank_base,
+                                                         w.item_base, w.cta_pair);
         threads = 2 * blocks_bound(ps.num_pairs, total, tile);
     } else {
         threads = 2 * ps.p_uniform * ps.num_pairs;
@@ -554,7 +564,7 @@ static BatchedWs sort_ws_layout(void* base, int64_t n, int64_t tile) {
         if (r > ranks) ranks = r;
         if (2 * ps.num_pairs * ps.p_uniform > items) items = 2 * ps.num_pairs * ps.p_uniform;
     }
-    return ws_layout(base, 0, ranks, items);
+    return ws_layout(base, 0, ranks, items, 0);
 }
 
 template <typename K>

@@ -31,11 +31,19 @@ inline size_t key_size(tm_key_type kt) { return (kt == TM_KEY_U64) ? 8 : 4; }
 // Block decomposition (Section 2)
 // ---------------------------------------------------------------------------
 
+// a / b for 0 <= a, 0 < b: a 32-bit division when both operands fit (the
+// usual case: blocks and tiles of one merge), else the full-width one.
+template <typename I>
+__host__ __device__ __forceinline__ I div_nonneg(I a, I b) {
+    if (sizeof(I) > 4 && ((uint64_t)a | (uint64_t)b) <= 0xffffffffull) return (I)((uint32_t)a / (uint32_t)b);
+    return a / b;
+}
+
 // x_i for 0 <= i <= p: i*ceil(len/p) for i < r = len mod p, else
 // i*floor(len/p) + r (so x_p = len).
 template <typename I>
 __host__ __device__ __forceinline__ I block_start(I len, I p, I i) {
-    I q = len / p, r = len - q * p;
+    I q = div_nonneg(len, p), r = len - q * p;
     return (i < r) ? i * (q + 1) : i * q + r;
 }
 
@@ -45,9 +53,9 @@ __host__ __device__ __forceinline__ I block_start(I len, I p, I i) {
 template <typename I>
 __host__ __device__ __forceinline__ I block_of(I len, I p, I k) {
     if (k >= len) return p;
-    I q = len / p, r = len - q * p;
+    I q = div_nonneg(len, p), r = len - q * p;
     I head = r * (q + 1);
-    return (k < head) ? k / (q + 1) : (k - head) / q + r;
+    return (k < head) ? div_nonneg(k, q + 1) : div_nonneg(k - head, q) + r;
 }
 
 // Smallest block index j whose start y_j is >= k (0 <= k <= len): the block
