@@ -255,34 +255,50 @@ def cpu_baseline(items):
 def bench_small_merge(dev, steps: int = 200):
     """The 1M merge: A n = 2**20, B m = 2**19 u32 keys in [0, 2**16), p = 1024
     blocks per input; one tm_merge captured in a CUDA graph and replayed (a
-    merge of 25 MB is launch-latency bound)."""
+    merge of 25 MB is launch-latency bound).  L2 is flushed (a 256 MB write)
+    before every timed replay; each replay is timed alone with CUDA events
+    and the median reported."""
     from paper_1202_6575_gb300 import tm, workloads as W
     A, Av, B, Bv = W.single_merge_1m(dev)
     n, m = A.numel(), B.numel()
-    cfg = {"p": 1024}
     C = torch.empty(n + m, dtype=torch.int32, device=dev)
     Cv = torch.empty(n + m, dtype=torch.int32, device=dev)
-    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s = torch.cuda.Stream(dev)
-    tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
-    s.synchronize()
-    with tm.Graph(s) as g:
+    out = {"workload": "A 2^20 + B 2^19 u32 keys in [0, 2^16), u32 payloads, p = 1024; one CUDA graph replay "
+                       "per merge", "elements": n + m, "unit": UNIT, "l2": "flushed before every replay"}
+    ref = None
+    graphs = []                          # kept alive: destroying a graph during a capture invalidates it
+    for name, cfg in (("fused", {"p": 1024}), ("separate_launches", {"p": 1024, "unfused": 1})):
+        ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
         tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
-    for _ in range(10):
-        g.launch()
-    s.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(steps):
-        g.launch()
-    e1.record(s)
-    e1.synchronize()
-    us = e0.elapsed_time(e1) * 1e3 / steps
-    assert tm.tm_read_status(ws, stream=s) == 0
-    return {"workload": "A 2^20 + B 2^19 u32 keys in [0, 2^16), u32 payloads, p = 1024; one CUDA graph replay "
-                        "per merge (memset, search, plan, memset, tile merge)",
-            "elements": n + m, "us_per_merge": us, "value": (n + m) / (us / 1e6), "unit": UNIT,
-            "gbs": (n + m) * 16 / (us / 1e6) / 1e9}
+        s.synchronize()
+        g = tm.Graph(s)
+        graphs.append(g)
+        with g:
+            tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
+        for _ in range(10):
+            g.launch()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(s):
+            for i, (e0, e1) in enumerate(evs):
+                flush.fill_(i & 255)
+                e0.record(s)
+                g.launch()
+                e1.record(s)
+        s.synchronize()
+        us = float(np.median([e0.elapsed_time(e1) * 1e3 for e0, e1 in evs]))
+        assert tm.tm_read_status(ws, stream=s) == 0
+        if ref is None:
+            ref = (C.clone(), Cv.clone())
+        else:
+            assert torch.equal(ref[0], C) and torch.equal(ref[1], Cv)
+        out[name] = {"us_per_merge": us, "value": (n + m) / (us / 1e6), "gbs": (n + m) * 16 / (us / 1e6) / 1e9,
+                     "graph": "memset, fused search + merge kernel" if name == "fused" else
+                              "memset, search, plan, memset, merge"}
+    out.update({"us_per_merge": out["fused"]["us_per_merge"], "value": out["fused"]["value"],
+                "gbs": out["fused"]["gbs"]})
+    return out
 
 
 def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = True, cfg=None):
@@ -345,7 +361,7 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
             "speedup_vs_plain": None if ms_plain is None else ms_plain / ms}
 
 
-def bench_sort(dev, steps: int = 3):
+def bench_sort(dev, steps: int = 3, cfg=None):
     """Stable merge sort of 2**28 u64 keys uniform in [0, 2**24) with u32
     payloads (original index): sorted runs of 1024, then 18 merge rounds."""
     from paper_1202_6575_gb300 import tm, workloads as W
@@ -356,7 +372,7 @@ def bench_sort(dev, steps: int = 3):
     big = max(tm.tm_merge_sort_workspace_size(n, {"tile": t}) for t in (1024, 2048, 4096))
     ws = tm.new_workspace(big, dev)
     s = torch.cuda.Stream(dev)
-    best = tm.tm_autotune_sort("u64", src_k, src_v, keys, vals, tk, tv, ws, stream=s)
+    best = cfg or tm.tm_autotune_sort("u64", src_k, src_v, keys, vals, tk, tv, ws, stream=s)
     times = []
     for _ in range(steps + 1):
         keys.copy_(src_k)
@@ -566,7 +582,9 @@ def main():
                                        ("split", args.split)) if v} or None
             out = bench_batched(dev, pairs=args.pairs, with_plain=args.pairs == 65536 and fixed is None, cfg=fixed)
         elif args.form == "sort":
-            out = bench_sort(dev)
+            fixed = {k: v for k, v in (("tile", args.tile), ("threads", args.threads), ("stages", args.stages),
+                                       ("split", args.split)) if v} or None
+            out = bench_sort(dev, cfg=fixed)
         elif args.form == "small":
             out = bench_small_merge(dev)
         elif args.form == "search":

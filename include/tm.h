@@ -82,8 +82,9 @@ typedef struct tm_config {
                            default 128 */
     int32_t grid;       /* CTAs of the persistent kernels; default: resident CTAs per SM
                            x SM count */
-    int32_t stages;     /* input stages of the persistent tile kernel (1, 2 or 4); default 2
-                           (1 when two do not fit in shared memory) */
+    int32_t stages;     /* input stages of the persistent tile kernel: 2, 3 or 4 with
+                           TM_SPLIT_DIAGONAL (default 4 when two CTAs fit on an SM, else 3,
+                           else 2), 1, 2 or 4 with TM_SPLIT_BLOCKS (default 2) */
     int32_t split;      /* how a CTA divides its staged tile among its threads:
                            TM_SPLIT_DIAGONAL (2; also 0 = default) or TM_SPLIT_BLOCKS (1) */
     int32_t wait_ms;    /* limit of every wait of the persistent tile kernel on a stage
@@ -93,7 +94,8 @@ typedef struct tm_config {
                            withholds the readiness signal of its test_drop_tile-th staged
                            tile, so its consumers' wait runs out (TM_ERR_TIMEOUT); the
                            merge result is then incomplete.  Exercises the bounded waits. */
-    int32_t reserved;
+    int32_t unfused;    /* tm_merge only: 1 forces the separate search, plan and merge
+                           launches where the fused single launch would be used (below) */
 } tm_config;
 
 /* In-CTA split modes.  TM_SPLIT_BLOCKS applies the paper's rule again inside
@@ -112,6 +114,11 @@ TM_API const char* tm_status_str(tm_status s);
 
 /* Library version, for the binding's load check. */
 TM_API int tm_version(void);
+
+/* Name of the CUDA error behind the calling thread's most recent
+ * TM_ERR_CUDA from a launch of this library ("cudaSuccess" if none was
+ * recorded; static storage). */
+TM_API const char* tm_last_cuda_error(void);
 
 /* ------------------------------------------------------------------------ */
 /* Device status word                                                        */
@@ -141,8 +148,16 @@ TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg
  * is the single synchronisation of Section 2, and Steps 3-4 run as a
  * planning kernel (one tile record per subproblem) and the persistent
  * staged tile-merge kernel.  Equivalent to tm_cross_ranks,
- * tm_plan_subproblems and tm_merge_tiles on the workspace's arrays.  The
- * status word (first 4 bytes of the workspace) is cleared by this call. */
+ * tm_plan_subproblems and tm_merge_tiles on the workspace's arrays.
+ * Small merges (p <= 16384 and default in-CTA settings: no cfg->threads,
+ * stages, grid, split other than the default, wait_ms or test_drop_tile)
+ * run instead as one cooperative launch of the tile kernel: its threads do
+ * the 2p + 1 searches, a grid-wide barrier (bounded wait: TM_ERR_TIMEOUT)
+ * stands for the synchronisation, and each CTA then derives the
+ * subproblems of the blocks it takes (Steps 3-4) and merges them; the
+ * result is identical and the tile records of the workspace are not
+ * written.  cfg->unfused = 1 keeps the separate launches.  The control
+ * block (status word in its first 4 bytes) is cleared by this call. */
 TM_API tm_status tm_merge(tm_key_type kt,
                    const void* a_keys, const uint32_t* a_vals, int64_t n,
                    const void* b_keys, const uint32_t* b_vals, int64_t m,

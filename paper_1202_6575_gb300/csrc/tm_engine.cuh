@@ -195,6 +195,15 @@ struct EngineArgs {
     uint64_t wait_ns;              // limit of every mbarrier wait
     int drop_fill;                 // testing: fill index whose readiness signal is withheld (-1: none)
     EngineLayout lay;
+    // Fused single merge (one cooperative launch): the kernel first computes
+    // the cross ranks fx[0..p], fy[0..p] of A (lenA) and B (lenB), waits at a
+    // grid barrier (gbar: arrival count, zero at launch), writes the records
+    // of the 2p blocks into desc (Steps 3-4 selection), waits again, then
+    // merges.
+    int64_t* fx;
+    int64_t* fy;
+    int64_t fp;
+    unsigned int* gbar;
 };
 
 // Bulk-copy window of elements [lo, lo+cnt) of an array (base, len,
@@ -259,6 +268,137 @@ __device__ __forceinline__ void store_out(const uint8_t* buf, const void* base, 
     }
 }
 
+// Steps 3-4 selection of block k of a single merge (A-side block k for k < p,
+// B-side block k - p otherwise): its subproblem from the five cases in
+// split-point form, written as the record at its merge-path (chain) index.
+// A-point P_A(i) has i A-points and first_block_at_or_after(m, p, xbar_i)
+// B-points before it, and symmetrically for P_B(j), so the chain index is a
+// sum of two O(1) terms.  Empty blocks (p above a length) write nothing; the
+// non-empty records fill indices [0, min(p, n) + min(p, m)).
+template <typename LoadX, typename LoadY>
+__device__ __forceinline__ void plan_single_record(int64_t n, int64_t m, int64_t p, int64_t k, LoadX xb, LoadY yb,
+                                                   TileDesc* desc) {
+    const bool a_side = k < p;
+    const int64_t pe = a_side ? k : k - p;
+    if (a_side ? block_start<int64_t>(n, p, pe) >= n : block_start<int64_t>(m, p, pe) >= m) return;
+    int64_t a0, a1, b0, b1;
+    subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
+    const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
+                                 : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
+    TileDesc d{};
+    d.a0 = a0; d.b0 = b0; d.c0 = a0 + b0;
+    d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);
+    d.first = chain == 0;
+    desc[chain] = d;
+}
+
+// Rank of x in sorted X[0..len) by one warp: each round the 32 lanes probe
+// 32 positions splitting the candidate range [lo, hi] into 33 parts and the
+// ballot of "X[q-1] lies before x" (true on a prefix of the lanes, X being
+// sorted) keeps one part; ceil(log33(len + 1)) rounds instead of
+// ceil(log2(len + 1)) dependent probes.  HIGH: rank_high (elements <= x),
+// else rank_low (elements < x).  Every lane returns the rank.
+template <bool HIGH, typename K>
+__device__ __forceinline__ int64_t warp_rank(const K* __restrict__ X, int64_t len, K x, int lane) {
+    int64_t lo = 0, hi = len;
+    while (hi > lo) {
+        const int64_t w = hi - lo;
+        const int64_t q = lo + (((int64_t)lane + 1) * w + 32) / 33;      // in (lo, hi]
+        const K v = __ldg(X + q - 1);
+        const bool before = HIGH ? !(x < v) : (v < x);
+        const int c = __popc(__ballot_sync(0xffffffffu, before));
+        const int64_t qlo = __shfl_sync(0xffffffffu, q, c > 0 ? c - 1 : 0);
+        const int64_t qhi = __shfl_sync(0xffffffffu, q, c < 32 ? c : 31);
+        lo = c > 0 ? qlo : lo;
+        hi = c < 32 ? qhi - 1 : hi;
+    }
+    return lo;
+}
+
+// Fused single merge, Steps 1-2: the 2p + 1 cross ranks, one warp per
+// search, strided over every warp of the grid (B-block starts first).
+template <typename K>
+__device__ __forceinline__ void fused_cross_ranks(const EngineArgs& g) {
+    const K* A = static_cast<const K*>(g.A);
+    const K* B = static_cast<const K*>(g.B);
+    const int64_t n = g.lenA, m = g.lenB, p = g.fp;
+    const int lane = threadIdx.x & 31;
+    const int64_t wpc = blockDim.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * wpc;
+    for (int64_t t = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); t <= 2 * p; t += stride) {
+        if (t < p) {
+            const int64_t yj = block_start<int64_t>(m, p, t);
+            const int64_t r = (yj < m) ? warp_rank<true, K>(A, n, __ldg(B + yj), lane) : n;
+            if (lane == 0) g.fy[t] = r;
+        } else if (t < 2 * p) {
+            const int64_t i = t - p;
+            const int64_t xi = block_start<int64_t>(n, p, i);
+            const int64_t r = (xi < n) ? warp_rank<false, K>(B, m, __ldg(A + xi), lane) : m;
+            if (lane == 0) g.fx[i] = r;
+        } else if (lane == 0) {
+            g.fx[p] = m;
+            g.fy[p] = n;
+        }
+    }
+}
+
+// Fused single merge, Steps 3-4 selection: every block's record, strided over
+// the grid's threads, into g.desc (the ranks were written in this launch, so
+// they are read through L2: ld.global.cg).
+__device__ __forceinline__ void fused_plan(const EngineArgs& g) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const long long* fx = reinterpret_cast<const long long*>(g.fx);
+    const long long* fy = reinterpret_cast<const long long*>(g.fy);
+    auto xb = [&](int64_t i) { return (int64_t)__ldcg(fx + i); };
+    auto yb = [&](int64_t j) { return (int64_t)__ldcg(fy + j); };
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * g.fp; k += stride)
+        plan_single_record(g.lenA, g.lenB, g.fp, k, xb, yb, const_cast<TileDesc*>(g.desc));
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident).  bar counts
+// arrivals over the whole launch (zero at launch): the k-th barrier of the
+// launch waits until it reaches k * gridDim.x.  Thread 0 arrives with a
+// release add after the CTA's barrier and polls with acquire loads (backing
+// off 64 ns between polls), at most limit_ns of global time (then
+// TM_ERR_TIMEOUT and false).  The same value for every thread of the CTA.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int k, uint64_t limit_ns, int32_t* status) {
+    __shared__ int passed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = k * gridDim.x;
+        unsigned int v;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+        int ok = 1;
+        if (v + 1 < target) {
+            const uint64_t t0 = global_timer_ns();
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+                if (v >= target) break;
+                if (global_timer_ns() - t0 > limit_ns) { ok = 0; set_status(status, TM_ERR_TIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        passed = ok;
+    }
+    __syncthreads();
+    return passed != 0;
+}
+
+// A work item's record: from the plan kernel's array, or, in the fused
+// launch, from the array this launch wrote (read through L2).
+template <bool FUSED>
+__device__ __forceinline__ TileDesc engine_record(const EngineArgs& g, int64_t q) {
+    if constexpr (FUSED) {
+        const int4* src = reinterpret_cast<const int4*>(g.desc + q);
+        TileDesc d;
+        int4* dst = reinterpret_cast<int4*>(&d);
+        dst[0] = __ldcg(src); dst[1] = __ldcg(src + 1); dst[2] = __ldcg(src + 2);
+        return d;
+    } else {
+        return g.desc[q];
+    }
+}
+
 // In-CTA split of a staged tile among the consumer threads:
 //   kSplitBlocks   - the paper's rule again: T blocks per piece, cross ranks
 //                    of the block starts, 2T sub-subproblems, two per thread,
@@ -276,7 +416,7 @@ enum { kSplitBlocks = 0, kSplitDiagonal = 1 };
 // `cap` elements (consecutive records are adjacent on the merge path).
 // Lanes 0..3 handle the four pieces (A keys, A payloads, B keys, B payloads)
 // in parallel; lane 0 writes the header and arms the stage's barrier.
-template <typename K, int LOG_T, int S_IN, int SPLIT>
+template <typename K, int LOG_T, int S_IN, int SPLIT, bool FUSED>
 __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                 uint64_t* empty, int lane) {
     int k = 0;                                        // fills issued
@@ -287,13 +427,13 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
     if (lane == 0) base = atomicAdd(g.queue, (unsigned long long)G);
     base = __shfl_sync(0xffffffffu, base, 0);
     TileDesc d{};
-    if (lane < G && base + lane < nitems) d = g.desc[base + lane];
+    if (lane < G && base + lane < nitems) d = engine_record<FUSED>(g, (int64_t)(base + lane));
     while (ok && base < nitems) {
         unsigned long long nbase = 0;                 // prefetch the next grab
         if (lane == 0) nbase = atomicAdd(g.queue, (unsigned long long)G);
         nbase = __shfl_sync(0xffffffffu, nbase, 0);
         TileDesc nd{};
-        if (lane < G && nbase + lane < nitems) nd = g.desc[nbase + lane];
+        if (lane < G && nbase + lane < nitems) nd = engine_record<FUSED>(g, (int64_t)(nbase + lane));
         const int avail = (int)min((unsigned long long)G, nitems - base);
         for (int q = 0; q < avail && ok;) {
             const int64_t a0 = __shfl_sync(0xffffffffu, d.a0, q);
@@ -533,7 +673,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
     if (leader) bulk_wait_read<0>();
 }
 
-template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT>
+template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT, bool FUSED = false>
 __global__ void __launch_bounds__((1 << LOG_T) + 32)
 merge_engine_kernel(const EngineArgs g) {
     constexpr int T = 1 << LOG_T;
@@ -547,8 +687,14 @@ merge_engine_kernel(const EngineArgs g) {
         fence_proxy_async_smem();
     }
     __syncthreads();
+    if constexpr (FUSED) {                            // Steps 1-2, the single synchronisation, the plan
+        fused_cross_ranks<K>(g);
+        if (!grid_barrier(g.gbar, 1, g.wait_ns, g.status)) return;
+        fused_plan(g);
+        if (!grid_barrier(g.gbar, 2, g.wait_ns, g.status)) return;
+    }
     if (tid >= T) {
-        engine_producer<K, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
+        engine_producer<K, LOG_T, S_IN, SPLIT, FUSED>(g, smem, full, empty, tid - T);
         return;
     }
     if constexpr (SPLIT == kSplitDiagonal) engine_consumers_diagonal<K, LOG_T, S_IN, VT>(g, smem, full, empty, tid);

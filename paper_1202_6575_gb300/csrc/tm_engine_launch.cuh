@@ -32,7 +32,8 @@ tm_status launch_engine_s(const EngineArgs& a_in, const tm_config* cfg, cudaStre
     if (grid < 1) grid = 1;
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return TM_ERR_CUDA;
     kern<<<(unsigned)grid, block, a.lay.total, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
 }
 
 // Paper's rule inside the CTA, with separate output buffers.  cfg->stages:
@@ -82,6 +83,79 @@ tm_status launch_diagonal(const EngineArgs& a, const tm_config* cfg, cudaStream_
     if (a.cap <= 9 * T) return launch_diagonal_vt<K, LOG_T, 9>(a, cfg, s);
     if (a.cap <= 17 * T) return launch_diagonal_vt<K, LOG_T, 17>(a, cfg, s);
     if (a.cap <= 33 * T) return launch_diagonal_vt<K, LOG_T, 33>(a, cfg, s);
+    return TM_ERR_UNSUPPORTED;
+}
+
+// Fused single merge: one cooperative launch (every CTA resident, so the
+// grid barrier after the searches cannot wait on an unscheduled CTA),
+// 128 consumer threads, diagonal split, 4 input stages.  The work queue and
+// the barrier words must be zero (the caller clears the control block).
+template <typename K, int VT>
+tm_status launch_fused_vt(const EngineArgs& a_in, cudaStream_t s) {
+    constexpr int LOG_T = 7;
+    EngineArgs a = a_in;
+    a.lay = make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, 4, 0);
+    a.wait_ns = kWaitLimitNs;
+    a.drop_fill = -1;
+    auto kern = merge_engine_kernel<K, LOG_T, 4, 0, kSplitDiagonal, VT, true>;
+    if (!ensure_smem_limit(kern, a.lay.total)) return TM_ERR_UNSUPPORTED;
+    const int block = (1 << LOG_T) + 32;
+    int per_sm = 0;
+    if (const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, a.lay.total);
+        e != cudaSuccess || per_sm < 1) {
+        if (e != cudaSuccess) { record_cuda_error(e); cudaGetLastError(); }
+        return TM_ERR_UNSUPPORTED;
+    }
+    const int64_t grid = (int64_t)per_sm * sm_count();
+    // one grab per CTA where possible: its records pack into fuller tiles
+    const int64_t g = (a.n_items + grid - 1) / grid;
+    a.grab = (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
+    // Under stream capture the cooperative kernel goes in as an explicit graph
+    // node (cooperative is a valid kernel-node attribute) after the stream's
+    // current capture dependencies, which it then replaces.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (const cudaError_t e = cudaStreamIsCapturing(s, &cs); e != cudaSuccess) return cuda_failed(e);
+    if (cs == cudaStreamCaptureStatusActive) {
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) return cuda_failed(e);
+        void* args[1] = {&a};
+        cudaKernelNodeParams kp = {};
+        kp.func = reinterpret_cast<void*>(kern);
+        kp.gridDim = dim3((unsigned)grid);
+        kp.blockDim = dim3((unsigned)block);
+        kp.sharedMemBytes = a.lay.total;
+        kp.kernelParams = args;
+        cudaGraphNode_t node = nullptr;
+        if ((e = cudaGraphAddKernelNode(&node, graph, deps, ndeps, &kp)) != cudaSuccess) return cuda_failed(e);
+        cudaKernelNodeAttrValue v = {};
+        v.cooperative = 1;
+        if ((e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v)) != cudaSuccess)
+            return cuda_failed(e);
+        e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        return e == cudaSuccess ? TM_OK : cuda_failed(e);
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3((unsigned)block);
+    lc.dynamicSmemBytes = a.lay.total;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, kern, a);
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
+}
+
+template <typename K>
+tm_status launch_engine_fused(const EngineArgs& a, cudaStream_t s) {
+    if (a.cap < 1) return TM_ERR_UNSUPPORTED;
+    if (a.cap <= 9 * 128) return launch_fused_vt<K, 9>(a, s);
+    if (a.cap <= 17 * 128) return launch_fused_vt<K, 17>(a, s);
     return TM_ERR_UNSUPPORTED;
 }
 

@@ -26,6 +26,14 @@ inline bool aligned(const void* p, size_t a) {
     return p != nullptr && (reinterpret_cast<uintptr_t>(p) % a) == 0;
 }
 
+// The CUDA error behind the calling thread's last TM_ERR_CUDA (see
+// tm_last_cuda_error); cuda_failed records it and returns TM_ERR_CUDA.
+void record_cuda_error(cudaError_t e);
+inline tm_status cuda_failed(cudaError_t e) {
+    record_cuda_error(e);
+    return TM_ERR_CUDA;
+}
+
 // Opt-in dynamic shared memory per CTA of the current device, capped at
 // kMaxSmemBytes.
 inline uint32_t device_smem_limit() {
@@ -35,24 +43,35 @@ inline uint32_t device_smem_limit() {
     return (uint32_t)v < kMaxSmemBytes ? (uint32_t)v : kMaxSmemBytes;
 }
 
-// Raises a kernel's dynamic shared-memory limit to the device maximum (once
-// per kernel and device); false if `bytes` does not fit.
+// Raises a kernel's dynamic shared-memory limit to the device maximum less
+// the kernel's static shared memory (once per kernel and device); false if
+// `bytes` does not fit.
 template <typename Kernel>
 inline bool ensure_smem_limit(Kernel kernel, uint32_t bytes) {
     static std::mutex mu;
     static std::unordered_map<const void*, uint64_t> done;   // kernel -> device mask
+    static std::unordered_map<const void*, uint32_t> limit;  // kernel -> its dynamic limit
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    const uint32_t lim = device_smem_limit();
-    if (lim == 0 || bytes > lim) return false;
     std::lock_guard<std::mutex> lock(mu);
-    uint64_t& mask = done[reinterpret_cast<const void*>(kernel)];
+    const void* key = reinterpret_cast<const void*>(kernel);
+    uint64_t& mask = done[key];
     if (!((mask >> dev) & 1ull)) {
-        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+        const uint32_t dev_lim = device_smem_limit();
+        const uint32_t lim = dev_lim > fa.sharedSizeBytes ? dev_lim - (uint32_t)fa.sharedSizeBytes : 0;
+        if (e == cudaSuccess && lim > 0)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess || lim == 0) {
+            if (e != cudaSuccess) record_cuda_error(e);
+            cudaGetLastError();                          // not sticky: later launches must not see it
             return false;
+        }
+        limit[key] = lim;                               // devices of one process share the part (sm_103a only)
         mask |= 1ull << dev;
     }
-    return true;
+    return bytes <= limit[key];
 }
 
 // Streaming multiprocessors of the current device (cached per device).

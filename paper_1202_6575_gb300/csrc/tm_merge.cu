@@ -10,6 +10,10 @@
 
 namespace pmerge {
 
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+void record_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+static cudaError_t last_cuda_error() { return g_last_cuda_error; }
+
 // ---------------------------------------------------------------------------
 // Steps 1-2: cross-rank search kernel
 // ---------------------------------------------------------------------------
@@ -72,20 +76,9 @@ plan_single_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restrict__ 
                    const int64_t* __restrict__ ybar, TileDesc* __restrict__ desc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 2 * p) return;
-    const bool a_side = k < p;
-    const int64_t pe = a_side ? k : k - p;
-    if (a_side ? block_start<int64_t>(n, p, pe) >= n : block_start<int64_t>(m, p, pe) >= m) return;
     auto xb = [&](int64_t i) { return __ldg(xbar + i); };
     auto yb = [&](int64_t j) { return __ldg(ybar + j); };
-    int64_t a0, a1, b0, b1;
-    subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
-    const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
-                                 : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
-    TileDesc d{};
-    d.a0 = a0; d.b0 = b0; d.c0 = a0 + b0;
-    d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);
-    d.first = chain == 0;
-    desc[chain] = d;
+    plan_single_record(n, m, p, k, xb, yb, desc);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,6 +241,12 @@ extern template tm_status launch_engine<uint32_t>(const EngineArgs&, const tm_co
 extern template tm_status launch_engine<int32_t>(const EngineArgs&, const tm_config*, cudaStream_t);
 extern template tm_status launch_engine<uint64_t>(const EngineArgs&, const tm_config*, cudaStream_t);
 extern template tm_status launch_engine<float>(const EngineArgs&, const tm_config*, cudaStream_t);
+template <typename K>
+tm_status launch_engine_fused(const EngineArgs& a, cudaStream_t s);
+extern template tm_status launch_engine_fused<uint32_t>(const EngineArgs&, cudaStream_t);
+extern template tm_status launch_engine_fused<int32_t>(const EngineArgs&, cudaStream_t);
+extern template tm_status launch_engine_fused<uint64_t>(const EngineArgs&, cudaStream_t);
+extern template tm_status launch_engine_fused<float>(const EngineArgs&, cudaStream_t);
 
 template <typename K>
 static tm_status merge_tiles_typed(const void* a_keys, const uint32_t* a_vals, int64_t n,
@@ -300,7 +299,7 @@ static int64_t single_merge_tiles(int64_t n, int64_t m, int64_t p) {
     return (n < p ? n : p) + (m < p ? m : p);
 }
 
-// Workspace of tm_merge: [status int32 | queue u64 | pad to 256] xbar ybar tiles.
+// Workspace of tm_merge: [status int32 | queue u64 | grid-barrier count u32 | pad to 256] xbar ybar tiles.
 struct MergeWs { int32_t* status; void* control; int64_t* xbar; int64_t* ybar; TileDesc* tiles; size_t bytes; };
 
 static MergeWs merge_ws_layout(void* base, int64_t p) {
@@ -318,19 +317,51 @@ static MergeWs merge_ws_layout(void* base, int64_t p) {
 
 size_t merge_workspace_bytes(int64_t p) { return merge_ws_layout(nullptr, p).bytes; }
 
+// The fused single launch applies to small merges with the default in-CTA
+// settings (it has one configuration: 128 consumer threads, diagonal split,
+// 4 stages) on a device that supports cooperative launches.
+constexpr int64_t kFusedMaxBlocks = 16384;
+constexpr int64_t kFusedMaxCap = 17 * 128;
+
+static bool fused_applies(int64_t p, int64_t cap, const tm_config* cfg) {
+    if (p > kFusedMaxBlocks || cap > kFusedMaxCap) return false;
+    if (cfg && (cfg->unfused || (cfg->threads && cfg->threads != 128) || cfg->stages || cfg->grid ||
+                (cfg->split && cfg->split != TM_SPLIT_DIAGONAL) || cfg->wait_ms || cfg->test_drop_tile))
+        return false;
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop;
+}
+
 template <typename K>
 static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
                              const void* b_keys, const uint32_t* b_vals, int64_t m,
                              void* c_keys, uint32_t* c_vals, void* ws, int64_t p,
                              const tm_config* cfg, cudaStream_t s) {
     MergeWs w = merge_ws_layout(ws, p);
-    if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    // status word, work-queue counter, grid-barrier count
+    if (cudaError_t e = cudaMemsetAsync(w.control, 0, 32, s); e != cudaSuccess) return cuda_failed(e);
     if (n + m == 0) return TM_OK;
     if (log2_threads(cfg) < 0) return TM_ERR_UNSUPPORTED;
     const int64_t cap = single_merge_cap(n, m, p);
     if (cap > kMaxTileElems) return TM_ERR_UNSUPPORTED;
     const K* A = static_cast<const K*>(a_keys);
     const K* B = static_cast<const K*>(b_keys);
+    if (fused_applies(p, cap, cfg)) {
+        EngineArgs a{};
+        a.desc = w.tiles;
+        a.n_items = single_merge_tiles(n, m, p); a.items_bound = a.n_items;
+        a.status = w.status;
+        a.queue = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(w.control) + 8);
+        a.A = a_keys; a.Av = a_vals; a.lenA = n;
+        a.B = b_keys; a.Bv = b_vals; a.lenB = m;
+        a.C = c_keys; a.Cv = c_vals;
+        a.cap = (int)cap;
+        a.fx = w.xbar; a.fy = w.ybar; a.fp = p;
+        a.gbar = reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(w.control) + 16);
+        const tm_status st = launch_engine_fused<K>(a, s);
+        if (st != TM_ERR_UNSUPPORTED) return st;       // else: the separate launches below
+    }
     tm_status st = launch_cross_ranks<K>(A, n, B, m, p, w.xbar, w.ybar, s);
     if (st != TM_OK) return st;
     st = launch_plan_single(n, m, p, w.xbar, w.ybar, w.tiles, s);
@@ -359,6 +390,8 @@ const char* tm_status_str(tm_status s) {
 }
 
 int tm_version(void) { return kVersion; }
+
+const char* tm_last_cuda_error(void) { return cudaGetErrorName(last_cuda_error()); }
 
 tm_status tm_read_status(const void* status, tm_stream_t stream) {
     if (!status) return TM_ERR_INVALID;

@@ -37,7 +37,7 @@ class TmConfig(ctypes.Structure):
     """struct tm_config of include/tm.h (0 = default in every field)."""
     _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
-                ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("unfused", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
@@ -53,6 +53,7 @@ _I64, _I32, _SZ, _P = ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_
 _SIGNATURES = {
     "tm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "tm_version": (ctypes.c_int, []),
+    "tm_last_cuda_error": (ctypes.c_char_p, []),
     "tm_read_status": (ctypes.c_int, [_P, _P]),
     "tm_merge_blocks": (_I64, [_I64, _I64, _P]),
     "tm_merge_workspace_size": (_SZ, [_I64, _I64, _P]),
@@ -124,9 +125,13 @@ def tm_version() -> int:
     return int(load().tm_version())
 
 
+def tm_last_cuda_error() -> str:
+    return load().tm_last_cuda_error().decode()
+
+
 def _check(code: int, where: str):
     if code != TM_OK:
-        raise TmError(code, where)
+        raise TmError(code, where + (f" [{tm_last_cuda_error()}]" if code == TM_ERR_CUDA else ""))
 
 
 def _cfg(cfg):
@@ -305,7 +310,7 @@ def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream
 # ---------------------------------------------------------------------------
 
 def _cfg_dict(c: TmConfig) -> dict:
-    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_ if f != "reserved"}
+    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_}
 
 
 def tm_merge_batched_workspace_size(num_pairs: int, total_a: int, total_b: int, cfg=None) -> int:
@@ -407,7 +412,10 @@ def tm_graph_destroy(g):
 class Graph:
     """Captures the tm_* calls made inside `with Graph(stream) as g:` on
     `stream` (a non-default torch.cuda.Stream, made current in the block)
-    into a CUDA graph; g.launch() replays them."""
+    into a CUDA graph; g.launch() replays them.  A Graph must not be
+    destroyed while another capture runs on the same thread (that
+    invalidates the capture): rebinding a name that holds the previous
+    Graph in `with Graph(s) as g:` does exactly that, so keep it alive."""
 
     def __init__(self, stream):
         self.stream = stream
