@@ -452,7 +452,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K* __restrict__ out_k,
                 uint32_t* __restrict__ out_v, int64_t n) {
-    __shared__ K sk[kSortRun];
+    __shared__ K sk[kSortRun + 1];                    // + 1: the merge step reads one past a run
     __shared__ uint32_t sv[kSortRun];
     const int t = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * kSortRun;
@@ -486,13 +486,16 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
         }
     }
     for (int w = kSortVT; w < kSortRun; w <<= 1) {
-        __syncthreads();                                  // previous level's reads are done
+        // a pair of runs of 2w <= 32 * kSortVT elements lies inside one warp's
+        // 288 outputs: those levels synchronise the warp only
+        const bool in_warp = 2 * w <= 32 * kSortVT;
+        if (in_warp) __syncwarp(); else __syncthreads();  // previous level's reads are done
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
             const int i = t * kSortVT + q;
             if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
         }
-        __syncthreads();
+        if (in_warp) __syncwarp(); else __syncthreads();
         const int d0 = t * kSortVT;                       // first output this thread owns
         const int lo = (d0 / (2 * w)) * (2 * w);          // start of its pair of runs (w = 9 * 2^k)
         const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
@@ -516,15 +519,16 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
             ok[q] = q < cnt;
-            if (q < cnt) {
+            if (q < cnt) {                                // branch-free: select, then one load each
                 const bool takeR = (j < nr) && ((i >= nl) || (kr < kl));
-                if (takeR) {
-                    k[q] = kr; v[q] = sv[mid + j]; ++j;
-                    kr = (j < nr) ? Rr[j] : kr;
-                } else {
-                    k[q] = kl; v[q] = sv[lo + i]; ++i;
-                    kl = (i < nl) ? L[i] : kl;
-                }
+                const int src = takeR ? mid + j : lo + i;
+                k[q] = takeR ? kr : kl;
+                v[q] = sv[src];
+                const K nk = sk[src + 1];                 // past a run's end: never selected
+                kr = takeR ? nk : kr;
+                kl = takeR ? kl : nk;
+                j += takeR ? 1 : 0;
+                i += takeR ? 0 : 1;
             }
         }
     }

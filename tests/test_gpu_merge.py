@@ -137,6 +137,42 @@ def test_distributions_small(dist, split):
         gpu_merge_check("i32", A, Av, B, Bv, cfg={"split": split})
 
 
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+@pytest.mark.parametrize("n,m,p", [(1, 0, 1), (0, 5, 3), (7, 300, 64), (300, 7, 64), (5000, 3001, 8),
+                                   (40000, 20000, 40), ((1 << 16) + 3, (1 << 15) - 1, 1024)])
+def test_fused_launch_matches_separate_launches(kt, n, m, p):
+    """Small merges run as one cooperative launch (searches, grid barrier,
+    selection, merge); cfg unfused = 1 forces the separate launches.  Both
+    must give the oracle's merge."""
+    A, Av, B, Bv = W.small_merge(n, m, kt, seed=n + 7 * m + p, alphabet=50)
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"p": p})
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"p": p, "unfused": 1})
+
+
+def test_fused_launch_in_cuda_graph_replayed():
+    A, Av, B, Bv = W.small_merge(60000, 45001, "u32", seed=11, alphabet=1000)
+    d = [t.to(DEV) for t in (A, Av, B, Bv)]
+    cfg = {"p": 512}
+    C = torch.empty(A.numel() + B.numel(), dtype=A.dtype, device=DEV)
+    Cv = torch.empty_like(C, dtype=torch.int32)
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(A.numel(), B.numel(), cfg), DEV)
+    s = torch.cuda.Stream()
+    tm.tm_merge("u32", *d, C, Cv, ws, cfg=cfg, stream=s)
+    s.synchronize()
+    g = tm.Graph(s)
+    with g:
+        tm.tm_merge("u32", *d, C, Cv, ws, cfg=cfg, stream=s)
+    K, V = oracle.merge_two_pointer(to_np(A, "u32"), vals_np(Av), to_np(B, "u32"), vals_np(Bv))
+    for _ in range(2):
+        C.fill_(-1)
+        Cv.fill_(-1)
+        torch.cuda.synchronize()
+        g.launch()
+        s.synchronize()
+        assert tm.tm_read_status(ws, stream=s) == 0
+        assert first_mismatch(to_np(C, "u32"), K) is None and first_mismatch(vals_np(Cv), V) is None
+
+
 def test_single_merge_1m_p1024():
     """n = 2**20, m = 2**19 u32 keys in [0, 2**16), p = 1024."""
     A, Av, B, Bv = W.single_merge_1m(DEV)
