@@ -246,10 +246,27 @@ def cpu_baseline(items):
         if "hC" in it:
             same = same and np.array_equal(it["hC"].numpy(), K.view(np.int32)) and \
                 np.array_equal(it["hCv"].numpy().view(np.uint32), V)
+    # second baseline: the paper's algorithm on every host core (one thread
+    # per processing element, p = cores), same merges
+    cores = os.cpu_count() or 1
+    dtp = 0.0
+    same_par = True
+    for it, (A, Av, B, Bv) in zip(items, hosts):
+        t0 = time.perf_counter()
+        Kp, Vp, _, _ = oracle.paper_merge_parallel(A, Av, B, Bv, cores, cores)
+        dtp += time.perf_counter() - t0
+        if "hC" in it:                                  # the e2e outputs, equal to the oracle's above
+            same_par = same_par and np.array_equal(it["hC"].numpy(), Kp.view(np.int32)) and \
+                np.array_equal(it["hCv"].numpy().view(np.uint32), Vp)
+        del Kp, Vp
     return {"value": elems / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "each of the eight merges once (the full workload, one pass), single-thread "
                       "two-pointer merge of oracle/tm_oracle.c", "seconds": dt,
-            "e2e_outputs_equal_oracle": bool(same)}
+            "e2e_outputs_equal_oracle": bool(same),
+            "paper_parallel": {"value": elems / dtp, "unit": UNIT, "cores": cores, "p": cores,
+                               "kind": "paper's algorithm on POSIX threads (oracle/paper_parallel.c)",
+                               "sample": "the same eight merges once", "seconds": dtp,
+                               "outputs_equal_e2e": bool(same_par)}}
 
 
 def bench_small_merge(dev, steps: int = 200):

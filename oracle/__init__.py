@@ -5,13 +5,17 @@ and the CPU-baseline leg of ``bench.py`` may import this package.  It shares
 no code with the GPU library (``paper_1202_6575_gb300``) and never imports it;
 the library never imports this package.
 
-Two parts:
+Three parts:
 
 * ``tm_oracle.c`` (plain C, single thread, loaded through ctypes): the rank
   primitives and block decomposition of Section 2, Steps 1-4 with the five
   cases (a)-(e), the textbook stable two-pointer merge, the rank-scatter merge
   built from the position formulas of Section 2, many independent merges, and
   the stable merge sort of Section 3.
+* ``paper_parallel.c`` (POSIX threads): a CPU baseline, not a reference: the
+  paper's algorithm with one thread per processing element, on the oracle's
+  searches, five cases and two-pointer merge (checked against them by the
+  tests; the benchmark times it beside the single-thread merge).
 * ``cdf.py`` (numpy, float64): the learned cross-rank model (piecewise-linear
   CDF plus a two-layer MLP) forward, loss, backward and Adam step.  This model
   is not in the paper; it proposes cross ranks that the exact search then
@@ -27,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tm_oracle.c")
+_SRC_PAR = os.path.join(_HERE, "paper_parallel.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -50,11 +55,11 @@ def build(force: bool = False) -> str:
     """Compile tm_oracle.c into oracle/_build/liboracle.so with gcc."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAR))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-pthread",
+                           "-o", tmp, _SRC, _SRC_PAR])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -86,6 +91,9 @@ def _load():
             f = getattr(_lib, f"orc_paper_merge_{s}")
             f.restype = None
             f.argtypes = [p, p, i64, p, p, i64, i64, p, p, p, p, p]
+            f = getattr(_lib, f"orc_paper_merge_parallel_{s}")
+            f.restype = ctypes.c_int
+            f.argtypes = [p, p, i64, p, p, i64, i64, i64, p, p, p, p]
             f = getattr(_lib, f"orc_merge_batched_{s}")
             f.restype = None
             f.argtypes = [i64, p, p, p, p, p, p, p, p]
@@ -202,6 +210,26 @@ def paper_merge(A, Av, B, Bv, p: int):
         _ptr(A), _ptr(Av), n, _ptr(B), _ptr(Bv), m, p,
         _ptr(C), _ptr(Cv), _ptr(xbar), _ptr(ybar), _ptr(table))
     return C, Cv, xbar, ybar, table
+
+
+def paper_merge_parallel(A, Av, B, Bv, p: int, threads: int):
+    """CPU baseline (paper_parallel.c): the paper's algorithm with one POSIX
+    thread per processing element (threads of them, PE t also taking
+    t + threads, ...): Steps 1-2, the synchronisation, Steps 3-4 and the
+    subproblem merges.  Returns (C, Cv, xbar, ybar)."""
+    A, B = _c(A), _c(B)
+    Av, Bv = _c(Av, np.uint32), _c(Bv, np.uint32)
+    n, m = len(A), len(B)
+    C = np.empty(n + m, dtype=A.dtype)
+    Cv = np.empty(n + m, dtype=np.uint32)
+    xbar = np.empty(p + 1, dtype=np.int64)
+    ybar = np.empty(p + 1, dtype=np.int64)
+    rc = getattr(_load(), f"orc_paper_merge_parallel_{_suffix(A)}")(
+        _ptr(A), _ptr(Av), n, _ptr(B), _ptr(Bv), m, p, threads,
+        _ptr(C), _ptr(Cv), _ptr(xbar), _ptr(ybar))
+    if rc != 0:
+        raise MemoryError("paper_merge_parallel: no memory for its thread table")
+    return C, Cv, xbar, ybar
 
 
 def merge_batched(a_off, A, Av, b_off, B, Bv):

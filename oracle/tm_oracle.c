@@ -8,8 +8,9 @@
  * code, header, table or helper with the CUDA library, and the library never
  * calls it.
  *
- * Everything is single-threaded, written for readability, and follows the
- * paper's notation:
+ * Everything here is single-threaded, written for readability, and follows
+ * the paper's notation (paper_parallel.c, a CPU baseline, runs the same
+ * steps on several threads):
  *   A[0..n), B[0..m)   non-decreasing inputs (Section 2), sentinels
  *                      A[-1] = -inf, A[n] = +inf are implied, never stored;
  *   rank_low(x, X)     the unique i with X[i-1] < x <= X[i]  (Section 2);
@@ -124,16 +125,21 @@ static void one_side_case(int64_t len_own, int64_t len_oth, int64_t p, int64_t i
     row[0] = xi; row[1] = xi1; row[2] = xb; row[3] = yj1; row[4] = c0; row[5] = 'd';
 }
 
+/* Subproblem k of the 2p: A-side PE k (Step 3) for k < p, else B-side PE
+ * k - p (Step 4, roles exchanged; row[4] = y_j + ybar_j, own start + own
+ * cross rank). */
+void orc_subproblem(int64_t n, int64_t m, int64_t p, int64_t k,
+                    const int64_t* xbar, const int64_t* ybar, int64_t* row)
+{
+    if (k < p) one_side_case(n, m, p, k, xbar, ybar, row);
+    else       one_side_case(m, n, p, k - p, ybar, xbar, row);
+}
+
 void orc_subproblems(int64_t n, int64_t m, int64_t p,
                      const int64_t* xbar, const int64_t* ybar, int64_t* table)
 {
-    for (int64_t i = 0; i < p; ++i)            /* Step 3 */
-        one_side_case(n, m, p, i, xbar, ybar, table + 6 * i);
-    for (int64_t j = 0; j < p; ++j) {          /* Step 4: roles exchanged */
-        int64_t* row = table + 6 * (p + j);
-        one_side_case(m, n, p, j, ybar, xbar, row);
-        /* row[4] = y_j + ybar_j already (own start + own cross rank). */
-    }
+    for (int64_t k = 0; k < 2 * p; ++k)
+        orc_subproblem(n, m, p, k, xbar, ybar, table + 6 * k);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -302,6 +302,27 @@ def test_paper_merge_random_larger(dtype):
         check_table(A, B, p, xbar, ybar, table)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_parallel_baseline_equals_oracle(dtype):
+    """The CPU baseline (the paper's algorithm on POSIX threads) against the
+    stable sort of the tagged concatenation and the sequential paper_merge's
+    cross ranks, for thread counts below, at and above p."""
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        n = int(rng.integers(0, 5000))
+        m = int(rng.integers(0, 5000))
+        p = int(rng.integers(1, 100))
+        threads = int(rng.choice([1, 2, 3, 8, p, p + 5]))
+        A = rand_sorted(rng, n, dtype, int(rng.choice([1, 5, 1000, 10**6])))
+        B = rand_sorted(rng, m, dtype, int(rng.choice([1, 5, 1000, 10**6])))
+        Av, Bv = payloads(n, m)
+        C, Cv, xbar, ybar = oracle.paper_merge_parallel(A, Av, B, Bv, p, threads)
+        K, V = stable_reference(A, B)
+        assert np.array_equal(C, K) and np.array_equal(Cv, V), (n, m, p, threads)
+        _, _, xs, ys, _ = oracle.paper_merge(A, Av, B, Bv, p)
+        assert np.array_equal(xbar, xs) and np.array_equal(ybar, ys)
+
+
 def test_all_equal_cross_ranks():
     # All keys equal: xbar_i = 0 (no B element is below), ybar_j = n.
     A = np.zeros(10, dtype=np.int32)
