@@ -34,6 +34,10 @@
  *    only the device can see (a subproblem larger than its staging buffer, a
  *    bounded wait that gave up) are written to a device status word that
  *    tm_read_status() returns; kernels never trap.
+ *  - A workspace (or model) belongs to one call at a time: calls that use the
+ *    same workspace must be ordered on the GPU (one stream, or events);
+ *    overlapping ones race on its status word, work-queue counter, barrier
+ *    count and arrays.
  *  - Lengths are element counts (int64_t, >= 0).  Empty inputs are valid.
  */
 #ifndef TM_H
