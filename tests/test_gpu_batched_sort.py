@@ -59,6 +59,22 @@ def test_batched_log_uniform_small(split):
     batched_check(a_off, A, Av, b_off, B, Bv, cfg={"split": split})
 
 
+def test_batched_mostly_empty_pairs():
+    """Long runs of empty pairs: a search/plan CTA can span more pairs than
+    its shared-memory window holds and then finds its pairs in global memory."""
+    rng = np.random.default_rng(4)
+    pairs = 6000
+    lens_a = np.where(rng.random(pairs) < 0.98, 0, rng.integers(1, 5000, pairs))
+    lens_b = np.where(rng.random(pairs) < 0.98, 0, rng.integers(1, 5000, pairs))
+    lens_a[:700] = 0
+    lens_b[:700] = 0
+    lens_a[1000] = 300000
+    lens_a[2000:3000] = 0                   # 1000 empty pairs between two tiny ones: one CTA spans them
+    lens_b[2000:3000] = 0
+    lens_a[1999], lens_b[1999], lens_a[3000], lens_b[3000] = 3, 2, 4, 1
+    batched_check(*csr_pairs(lens_a, lens_b, "u64", 9), kt="u64", cfg={"tile": 256})
+
+
 def test_batched_no_pairs_and_all_empty():
     z = torch.zeros(1, dtype=torch.int64)
     e = torch.empty(0, dtype=torch.int64)

@@ -149,6 +149,15 @@ def test_fused_launch_matches_separate_launches(kt, n, m, p):
     gpu_merge_check(kt, A, Av, B, Bv, cfg={"p": p, "unfused": 1})
 
 
+@pytest.mark.parametrize("kt,log2n,p", [("u64", 20, 1024), ("i32", 20, 1024), ("f32", 24, 16384)])
+def test_fused_launch_full_tiles(kt, log2n, p):
+    """Subproblems up to 2048 elements (the 17-element runs of the fused
+    kernel) and the largest p the fused launch takes."""
+    n = 1 << log2n
+    A, Av, B, Bv = W.small_merge(n, n, kt, seed=log2n + p, alphabet=1 << 20)
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"p": p})
+
+
 def test_fused_launch_in_cuda_graph_replayed():
     A, Av, B, Bv = W.small_merge(60000, 45001, "u32", seed=11, alphabet=1000)
     d = [t.to(DEV) for t in (A, Av, B, Bv)]
