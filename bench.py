@@ -318,6 +318,35 @@ def bench_small_merge(dev, steps: int = 200):
     return out
 
 
+def bench_keys_only(dev, steps: int = 20):
+    """Keys-only merges (payload pointers NULL): n = m = 2**28 int32 keys,
+    uniform in [0, 1024) and uniform over int32; 8 B per output element moved
+    instead of 16.  tm_merge through the C ABI, median of `steps` calls."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    out = {"workload": "n = m = 2^28 int32 keys, no payloads", "unit": UNIT}
+    for dist in ("uniform_1024", "uniform_full"):
+        A, _, B, _ = W.large_merge(dist, False, dev)
+        n, m = A.numel(), B.numel()
+        C = torch.empty(n + m, dtype=torch.int32, device=dev)
+        ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m), dev)
+        tm.tm_merge("i32", A, None, B, None, C, None, ws)
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tm.tm_merge("i32", A, None, B, None, C, None, ws)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        assert tm.tm_read_status(ws) == 0
+        ms = float(np.median(ts))
+        gbs = (n + m) * 8 / (ms / 1e3) / 1e9
+        out[dist] = {"ms": ms, "value": (n + m) / (ms / 1e3), "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0]}
+        del A, B, C, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = True, cfg=None):
     """Batched form: 65,536 independent pairs (lengths log-uniform in
     [1, 2**16] per side, u64 keys + u32 payloads), autotuned, captured in a
@@ -576,7 +605,7 @@ def main():
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
-    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search"],
+    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
     ap.add_argument("--pairs", type=int, default=65536, help="batched form: pairs (profiling)")
@@ -606,6 +635,8 @@ def main():
             out = bench_small_merge(dev)
         elif args.form == "search":
             out = bench_search(dev, log2_base=args.log2_base)
+        elif args.form == "keys":
+            out = bench_keys_only(dev)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)
@@ -797,7 +828,7 @@ def main():
             it.clear()
         torch.cuda.empty_cache()
         forms = {"merge_1m_p1024": bench_small_merge(dev), "batched": bench_batched(dev),
-                 "merge_sort": bench_sort(dev)}
+                 "merge_sort": bench_sort(dev), "keys_only": bench_keys_only(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
     if rank == 0:

@@ -34,6 +34,12 @@
  *    only the device can see (a subproblem larger than its staging buffer, a
  *    bounded wait that gave up) are written to a device status word that
  *    tm_read_status() returns; kernels never trap.
+ *  - Keys-only merges: every merge and sort call accepts NULL for all of its
+ *    payload pointers (a_vals, b_vals and c_vals together; vals and tmp_vals
+ *    together for the sort) and then moves keys only (half the bytes for
+ *    4-byte keys).  A mix of NULL and non-NULL payload pointers is
+ *    TM_ERR_INVALID; tm_merge_noalloc, and cfg->split = TM_SPLIT_BLOCKS,
+ *    return TM_ERR_UNSUPPORTED for keys only.
  *  - A workspace (or model) belongs to one call at a time: calls that use the
  *    same workspace must be ordered on the GPU (one stream, or events);
  *    overlapping ones race on its status word, work-queue counter, barrier

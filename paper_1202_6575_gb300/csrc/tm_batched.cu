@@ -457,7 +457,10 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
     const int t = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * kSortRun;
     const int len = (int)(n - base < kSortRun ? n - base : kSortRun);
-    for (int i = t; i < len; i += kSortThreads) { sk[i] = in_k[base + i]; sv[i] = in_v[base + i]; }
+    for (int i = t; i < len; i += kSortThreads) {      // no payloads (keys-only sort): sv unused
+        sk[i] = in_k[base + i];
+        if (in_v) sv[i] = in_v[base + i];
+    }
     __syncthreads();
     // blocked registers: thread t holds elements [8t, 8t + 8); missing ones
     // (past len) are marked invalid and sort to the end
@@ -539,7 +542,10 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
         if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
     }
     __syncthreads();
-    for (int i = t; i < len; i += kSortThreads) { out_k[base + i] = sk[i]; out_v[base + i] = sv[i]; }
+    for (int i = t; i < len; i += kSortThreads) {
+        out_k[base + i] = sk[i];
+        if (out_v) out_v[base + i] = sv[i];
+    }
 }
 
 
@@ -635,9 +641,8 @@ tm_status check_batched(tm_key_type kt, int64_t pairs, const int64_t* a_off, con
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (pairs > 0 && (!aligned(a_off, 8) || !aligned(b_off, 8))) return TM_ERR_INVALID;
-    if ((total_a > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
-        (total_b > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
-        (total_a + total_b > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+    if ((total_a > 0 && !aligned(a_keys, E)) || (total_b > 0 && !aligned(b_keys, E)) ||
+        (total_a + total_b > 0 && !aligned(c_keys, E)) || !payloads_ok(total_a, a_vals, total_b, b_vals, c_vals))
         return TM_ERR_INVALID;
     return TM_OK;
 }
@@ -690,8 +695,9 @@ tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, v
     if (n < 0) return TM_ERR_INVALID;
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
-    if (n > 0 && (!aligned(keys, E) || !aligned(vals, 4) || !aligned(tmp_keys, E) || !aligned(tmp_vals, 4)))
-        return TM_ERR_INVALID;
+    if (n > 0 && (!aligned(keys, E) || !aligned(tmp_keys, E) ||
+                  ((vals || tmp_vals) && (!aligned(vals, 4) || !aligned(tmp_vals, 4)))))
+        return TM_ERR_INVALID;                      // vals and tmp_vals both NULL: keys only
     tm_config tuned;
     if (!cfg && tuned_config(2, kt, n, &tuned)) cfg = &tuned;
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < tm_merge_sort_workspace_size(n, cfg))
@@ -792,8 +798,9 @@ tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t*
     if (n < 0) return TM_ERR_INVALID;
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
-    if (n > 0 && (!aligned(src_keys, E) || !aligned(src_vals, 4) || !aligned(keys, E) || !aligned(vals, 4) ||
-                  !aligned(tmp_keys, E) || !aligned(tmp_vals, 4)))
+    if (n > 0 && (!aligned(src_keys, E) || !aligned(keys, E) || !aligned(tmp_keys, E) ||
+                  ((src_vals || vals || tmp_vals) &&
+                   (!aligned(src_vals, 4) || !aligned(vals, 4) || !aligned(tmp_vals, 4)))))
         return TM_ERR_INVALID;
     if (!workspace || !aligned(workspace, 256)) return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -474,7 +474,9 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
             const bool isB = lane >= 2, isV = (lane & 1) != 0;
             const uint32_t E = isV ? 4u : (uint32_t)sizeof(K);
             const void* pbase = isB ? (isV ? (const void*)g.Bv : g.B) : (isV ? (const void*)g.Av : g.A);
-            const int64_t plen = isB ? g.lenB : g.lenA, plo = isB ? b0 : a0, pcnt = isB ? nB : nA;
+            // keys-only merge (no payload arrays): the payload pieces are empty
+            const int64_t plen = isB ? g.lenB : g.lenA, plo = isB ? b0 : a0;
+            const int64_t pcnt = (isV && g.Cv == nullptr) ? 0 : (isB ? nB : nA);
             uint8_t* region = st + (isV ? g.lay.vals_off : g.lay.keys_off);
             uint32_t dst_off = 0;
             if (isB) {   // after the A piece of the same region, on a 16-byte boundary
@@ -602,7 +604,7 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
 // Consumers, equal output runs of VT elements per thread, results written
 // back into the consumed stage.  The stage is released one tile later, once
 // its bulk store has read it.
-template <typename K, int LOG_T, int S_IN, int VT>
+template <typename K, int LOG_T, int S_IN, int VT, bool VALS>
 __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                           uint64_t* empty, int tid) {
     constexpr int T = 1 << LOG_T;
@@ -626,6 +628,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         const int L = nA + nB;
         const int d0 = tid * VT;
         const int cnt = max(0, min(VT, L - d0));
+        constexpr bool vals = VALS;                    // false: keys-only merge
         K rk[VT];
         uint32_t rv[VT];
         if (cnt > 0) {
@@ -640,7 +643,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
                     const K* ks = takeB ? kB : kA;
                     const uint32_t* vs = takeB ? vB : vA;
                     rk[q] = takeB ? kb : ka;
-                    rv[q] = vs[idx];
+                    if constexpr (vals) rv[q] = vs[idx];
                     const K nxt = ks[idx + 1];
                     if (takeB) { kb = nxt; ++j; } else { ka = nxt; ++i; }
                 }
@@ -655,12 +658,15 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         uint32_t* oV = reinterpret_cast<uint32_t*>(bv + (gv & 15));
 #pragma unroll
         for (int q = 0; q < VT; ++q) {
-            if (q < cnt) { oK[d0 + q] = rk[q]; oV[d0 + q] = rv[q]; }
+            if (q < cnt) {
+                oK[d0 + q] = rk[q];
+                if constexpr (vals) oV[d0 + q] = rv[q];
+            }
         }
         fence_proxy_async_smem();
         consumer_sync(T);
         store_out<K>(bk, g.C, c0, L, tid, T, leader);
-        store_out<uint32_t>(bv, g.Cv, c0, L, tid, T, leader);
+        if constexpr (vals) store_out<uint32_t>(bv, g.Cv, c0, L, tid, T, leader);
         if (leader) {
             bulk_commit();
             if (pending >= 0) {                         // previous tile's store has read its stage
@@ -697,8 +703,11 @@ merge_engine_kernel(const EngineArgs g) {
         engine_producer<K, LOG_T, S_IN, SPLIT, FUSED>(g, smem, full, empty, tid - T);
         return;
     }
-    if constexpr (SPLIT == kSplitDiagonal) engine_consumers_diagonal<K, LOG_T, S_IN, VT>(g, smem, full, empty, tid);
-    else                                   engine_consumers_blocks<K, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
+    if constexpr (SPLIT == kSplitDiagonal) {           // payloads or keys only: one branch per launch
+        if (g.Cv != nullptr) engine_consumers_diagonal<K, LOG_T, S_IN, VT, true>(g, smem, full, empty, tid);
+        else                 engine_consumers_diagonal<K, LOG_T, S_IN, VT, false>(g, smem, full, empty, tid);
+    }
+    else engine_consumers_blocks<K, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
 }
 
 }  // namespace pmerge

@@ -164,6 +164,12 @@ tm_status launch_engine(const EngineArgs& a, const tm_config* cfg, cudaStream_t 
     if (a.cap < 1 || a.cap > kMaxTileElems) return TM_ERR_UNSUPPORTED;
     const int split = (cfg && cfg->split) ? cfg->split : TM_SPLIT_DEFAULT;
     const int lt = log2_threads(cfg);
+    if (a.Cv == nullptr) {                         // keys only: the diagonal split alone handles it
+        if (split != TM_SPLIT_DIAGONAL) return TM_ERR_UNSUPPORTED;
+        if (lt == 7 && a.cap <= 33 * 128) return launch_diagonal<K, 7>(a, cfg, s);
+        if (lt == 8 && a.cap <= 33 * 256) return launch_diagonal<K, 8>(a, cfg, s);
+        return TM_ERR_UNSUPPORTED;
+    }
     if (split == TM_SPLIT_BLOCKS) {
         switch (lt) {
             case 7: return launch_blocks<K, 7>(a, cfg, s);

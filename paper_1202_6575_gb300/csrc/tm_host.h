@@ -34,6 +34,15 @@ inline tm_status cuda_failed(cudaError_t e) {
     return TM_ERR_CUDA;
 }
 
+// Payload arguments of a merge of n and m elements into C: all three
+// arrays (each 4-byte aligned when its side is not empty), or, for a
+// keys-only merge, none (the output payload pointer NULL, and so the input
+// ones).
+inline bool payloads_ok(int64_t n, const void* a, int64_t m, const void* b, const void* c) {
+    if (c == nullptr) return a == nullptr && b == nullptr;
+    return (n == 0 || aligned(a, 4)) && (m == 0 || aligned(b, 4)) && aligned(c, 4);
+}
+
 // Opt-in dynamic shared memory per CTA of the current device, capped at
 // kMaxSmemBytes.
 inline uint32_t device_smem_limit() {

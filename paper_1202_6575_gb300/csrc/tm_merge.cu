@@ -421,9 +421,8 @@ tm_status tm_merge(tm_key_type kt,
     if (n < 0 || m < 0) return TM_ERR_INVALID;
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
-    if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
-        (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
-        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))))
+    if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
+        !payloads_ok(n, a_vals, m, b_vals, c_vals))
         return TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p))
@@ -488,10 +487,8 @@ tm_status tm_merge_tiles(tm_key_type kt,
     if (n < 0 || m < 0 || n_tiles < 0 || cap < 1 || !aligned(control, 256)) return TM_ERR_INVALID;
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
-    if ((n > 0 && (!aligned(a_keys, E) || !aligned(a_vals, 4))) ||
-        (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
-        (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))) ||
-        (n_tiles > 0 && !aligned(tiles, 16)))
+    if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
+        !payloads_ok(n, a_vals, m, b_vals, c_vals) || (n_tiles > 0 && !aligned(tiles, 16)))
         return TM_ERR_INVALID;
     if (n_tiles == 0 || n + m == 0) return TM_OK;
     return merge_tiles_dispatch(kt, a_keys, a_vals, n, b_keys, b_vals, m, tiles, n_tiles, cap,
@@ -593,7 +590,7 @@ extern "C" tm_status tm_merge_noalloc(tm_key_type kt,
         (m > 0 && (!aligned(b_keys, E) || !aligned(b_vals, 4))) ||
         (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))) ||
         (status && !aligned(status, 4)))
-        return TM_ERR_INVALID;
+        return c_vals == nullptr && a_vals == nullptr && b_vals == nullptr ? TM_ERR_UNSUPPORTED : TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
     if (p > kNoAllocMaxBlocks) return TM_ERR_WORKSPACE;   // beyond the built-in array
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -151,7 +151,9 @@ def _stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _dev(t: torch.Tensor, name: str, dtypes=None) -> int:
+def _dev(t, name: str, dtypes=None) -> int:
+    if t is None:                       # optional array (payloads of a keys-only call)
+        return 0
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
@@ -186,14 +188,16 @@ def new_workspace(nbytes: int, device) -> torch.Tensor:
 
 def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, stream=None):
     """Stable merge of (A, Av) and (B, Bv); returns (C, Cv, workspace).
-    The status word is the first 4 bytes of the workspace (tm_read_status)."""
+    Av = Bv = None merges keys only (Cv None).  The status word is the first
+    4 bytes of the workspace (tm_read_status)."""
     kd = TORCH_KEY_DTYPES[kt]
     n, m = A.numel(), B.numel()
     if C is None:
         C = torch.empty(n + m, dtype=A.dtype, device=A.device)
-    if Cv is None:
+    keys_only = Av is None and Bv is None
+    if Cv is None and not keys_only:
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
-    if C.numel() != n + m or Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m:
+    if C.numel() != n + m or (not keys_only and (Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m)):
         raise ValueError("length mismatch")
     cfgp = _cfg(cfg)
     if workspace is None:
@@ -250,7 +254,7 @@ def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None,
     n, m = A.numel(), B.numel()
     if C is None:
         C = torch.empty(n + m, dtype=A.dtype, device=A.device)
-    if Cv is None:
+    if Cv is None and (Av is not None or Bv is not None):
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
     if control is None:
         control = torch.zeros(256, dtype=torch.uint8, device=A.device)
@@ -325,7 +329,7 @@ def _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv):
     ta, tb = A.numel(), B.numel()
     if C is None:
         C = torch.empty(ta + tb, dtype=A.dtype, device=A.device)
-    if Cv is None:
+    if Cv is None and (Av is not None or Bv is not None):
         Cv = torch.empty(ta + tb, dtype=torch.int32, device=A.device)
     args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av"), ta,
             _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv"), tb,
@@ -355,7 +359,7 @@ def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=N
     n = keys.numel()
     if tmp_keys is None:
         tmp_keys = torch.empty_like(keys)
-    if tmp_vals is None:
+    if tmp_vals is None and vals is not None:    # vals None: keys-only sort
         tmp_vals = torch.empty_like(vals)
     if workspace is None:
         workspace = new_workspace(tm_merge_sort_workspace_size(n, cfg), keys.device)
@@ -542,7 +546,7 @@ def tm_merge_learned(model: CdfModel, A, Av, B, Bv, C=None, Cv=None, workspace=N
     n, m = A.numel(), B.numel()
     if C is None:
         C = torch.empty(n + m, dtype=torch.float32, device=A.device)
-    if Cv is None:
+    if Cv is None and (Av is not None or Bv is not None):
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
     if workspace is None:
         workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)

@@ -69,3 +69,12 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.tm_plan_tile_count(10, 3, 5) == 5 + 3
     assert lib.tm_merge_tile_cap(10, 7, 3) == 4 + 3
     assert lib.tm_rank_search(0, 2, P(16), 4, P(16), 4, P(64), None) == tm.TM_ERR_INVALID
+    # payload pointers: all three or none (keys only); a mix is rejected
+    assert lib.tm_merge(0, P(16), P(16), 3, P(32), None, 1, P(64), P(64), P(256), 1 << 20, None, None) == tm.TM_ERR_INVALID
+    assert lib.tm_merge(0, P(16), None, 3, P(32), None, 1, P(64), P(64), P(256), 1 << 20, None, None) == tm.TM_ERR_INVALID
+    assert lib.tm_merge(0, P(16), P(16), 3, P(32), P(32), 1, P(64), None, P(256), 1 << 20, None, None) == tm.TM_ERR_INVALID
+    # keys only passes the argument checks (here: the missing workspace is reported next)
+    assert lib.tm_merge(0, P(16), None, 3, P(32), None, 1, P(64), None, None, 0, None, None) == tm.TM_ERR_WORKSPACE
+    # the allocation-free entry point has no keys-only form
+    assert lib.tm_merge_noalloc(0, P(16), None, 3, P(32), None, 1, P(64), None, None, None, None) == \
+        tm.TM_ERR_UNSUPPORTED

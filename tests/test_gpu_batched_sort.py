@@ -75,6 +75,20 @@ def test_batched_mostly_empty_pairs():
     batched_check(*csr_pairs(lens_a, lens_b, "u64", 9), kt="u64", cfg={"tile": 256})
 
 
+def test_keys_only_batched_and_sort():
+    a_off, A, Av, b_off, B, Bv = W.batched_pairs("cpu", pairs=2000, log2_max=12, seed=31)
+    d = lambda t: t.to(DEV)
+    C, Cv, ws = tm.tm_merge_batched("u64", d(a_off), d(A), None, d(b_off), d(B), None)
+    assert Cv is None and tm.tm_read_status(ws) == 0
+    K, _ = oracle.merge_batched(a_off.numpy(), to_np(A, "u64"), vals_np(Av), b_off.numpy(), to_np(B, "u64"),
+                                vals_np(Bv))
+    assert first_mismatch(to_np(C, "u64"), K) is None
+    keys, vals = W.sort_input("cpu", n=(1 << 18) + 333, key_bits=12)
+    sk, sv, ws = tm.tm_merge_sort("u64", keys.to(DEV).clone(), None)
+    assert sv is None and tm.tm_read_status(ws) == 0
+    assert np.array_equal(to_np(sk, "u64"), np.sort(to_np(keys, "u64"), kind="stable"))
+
+
 def test_batched_no_pairs_and_all_empty():
     z = torch.zeros(1, dtype=torch.int64)
     e = torch.empty(0, dtype=torch.int64)

@@ -158,6 +158,19 @@ def test_fused_launch_full_tiles(kt, log2n, p):
     gpu_merge_check(kt, A, Av, B, Bv, cfg={"p": p})
 
 
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+@pytest.mark.parametrize("n,m,cfg", [(5000, 3001, {"p": 8}), (200003, 150001, None),
+                                     (70001, 50003, {"tile": 4096, "threads": 256}), (0, 9, None)])
+def test_keys_only_merge(kt, n, m, cfg):
+    """Payload pointers NULL: keys alone are merged (fused and separate
+    launches, several tile shapes); the keys equal the oracle's."""
+    A, Av, B, Bv = W.small_merge(n, m, kt, seed=n + m, alphabet=300)
+    C, Cv, ws = tm.tm_merge(kt, A.to(DEV), None, B.to(DEV), None, cfg=cfg)
+    assert Cv is None and tm.tm_read_status(ws) == 0
+    K, _ = oracle.merge_two_pointer(to_np(A, kt), vals_np(Av), to_np(B, kt), vals_np(Bv))
+    assert first_mismatch(to_np(C, kt), K) is None
+
+
 def test_fused_launch_in_cuda_graph_replayed():
     A, Av, B, Bv = W.small_merge(60000, 45001, "u32", seed=11, alphabet=1000)
     d = [t.to(DEV) for t in (A, Av, B, Bv)]
