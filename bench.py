@@ -318,6 +318,43 @@ def bench_small_merge(dev, steps: int = 200):
     return out
 
 
+def bench_partition(dev, reps: int = 5):
+    """Ablation: the eight large merges partitioned by the paper's blocks
+    (cross ranks of block starts, the five cases; the default) and by equal
+    output ranges (one co-rank search per 2048 outputs, prior work the paper
+    discusses), each through tm_merge; median of `reps` calls per merge."""
+    from paper_1202_6575_gb300 import tm
+    items = make_inputs(dev, 28, None, True)
+    out = {"workload": "the eight large merges (n = m = 2^28 and n = 2^28, m = 2^18 int32 keys + payloads)",
+           "unit": "ms"}
+    for name, cfg in (("blocks", {"partition": 0, "unfused": 1}), ("equal_output", {"partition": 1})):
+        per = {}
+        for it in items:
+            A, Av, B, Bv = it["A"], it["Av"], it["B"], it["Bv"]
+            n, m = A.numel(), B.numel()
+            C = torch.empty(n + m, dtype=torch.int32, device=dev)
+            Cv = torch.empty(n + m, dtype=torch.int32, device=dev)
+            ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
+            tm.tm_merge("i32", A, Av, B, Bv, C, Cv, ws, cfg=cfg)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                tm.tm_merge("i32", A, Av, B, Bv, C, Cv, ws, cfg=cfg)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            assert tm.tm_read_status(ws) == 0
+            per[it["name"]] = float(np.median(ts))
+            del C, Cv, ws
+        out[name] = {"total_ms": sum(per.values()), "per_merge_ms": per}
+    out["equal_output_over_blocks"] = out["equal_output"]["total_ms"] / out["blocks"]["total_ms"]
+    for it in items:
+        it.clear()
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_keys_only(dev, steps: int = 20):
     """Keys-only merges (payload pointers NULL): n = m = 2**28 int32 keys,
     uniform in [0, 1024) and uniform over int32; 8 B per output element moved
@@ -605,7 +642,8 @@ def main():
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
-    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys"],
+    ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys",
+                                                   "partition"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
     ap.add_argument("--pairs", type=int, default=65536, help="batched form: pairs (profiling)")
@@ -637,6 +675,8 @@ def main():
             out = bench_search(dev, log2_base=args.log2_base)
         elif args.form == "keys":
             out = bench_keys_only(dev)
+        elif args.form == "partition":
+            out = bench_partition(dev)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)
@@ -828,7 +868,8 @@ def main():
             it.clear()
         torch.cuda.empty_cache()
         forms = {"merge_1m_p1024": bench_small_merge(dev), "batched": bench_batched(dev),
-                 "merge_sort": bench_sort(dev), "keys_only": bench_keys_only(dev)}
+                 "merge_sort": bench_sort(dev), "keys_only": bench_keys_only(dev),
+                 "partition_ablation": bench_partition(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
     if rank == 0:

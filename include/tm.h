@@ -106,7 +106,19 @@ typedef struct tm_config {
                            merge result is then incomplete.  Exercises the bounded waits. */
     int32_t unfused;    /* tm_merge only: 1 forces the separate search, plan and merge
                            launches where the fused single launch would be used (below) */
+    int32_t partition;  /* tm_merge only: TM_PARTITION_BLOCKS (0, the paper's method) or
+                           TM_PARTITION_DIAGONALS (1, an ablation: equal output ranges) */
+    int32_t reserved;
 } tm_config;
+
+/* How tm_merge divides the merge into subproblems.  TM_PARTITION_BLOCKS is
+ * the paper's (Section 2): p blocks per input, cross ranks of the block
+ * starts, the five cases.  TM_PARTITION_DIAGONALS, kept as an ablation, cuts
+ * the output into equal ranges of `tile` elements instead (the equal-output
+ * partitioning of prior work the paper discusses in Section 1): one search
+ * per cut along its output diagonal (the co-rank i with B[d-i-1] < A[i] and
+ * A[i-1] <= B[d-i]), then the same tile merge.  Same result. */
+enum { TM_PARTITION_BLOCKS = 0, TM_PARTITION_DIAGONALS = 1 };
 
 /* In-CTA split modes.  TM_SPLIT_BLOCKS applies the paper's rule again inside
  * the CTA: `threads` blocks per piece, rank_low of every A-block start in the

@@ -82,6 +82,45 @@ plan_single_kernel(int64_t n, int64_t m, int64_t p, const int64_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Ablation: equal-output partitioning (prior work, Section 1) instead of the
+// paper's blocks.  Cut k sits at output diagonal d_k = min(k * tile, n + m);
+// its co-rank is the number of A elements among the first d_k outputs of the
+// stable merge, the i with B[d-i-1] < A[i] and A[i-1] <= B[d-i] (the position
+// formulas of Section 2), found by bisection along the diagonal.
+// ---------------------------------------------------------------------------
+
+template <typename K>
+__global__ void __launch_bounds__(256)
+diagonal_corank_kernel(const K* __restrict__ A, int64_t n, const K* __restrict__ B, int64_t m, int64_t tile,
+                       int64_t cuts, int64_t* __restrict__ corank) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > cuts) return;
+    const int64_t d = k * tile < n + m ? k * tile : n + m;
+    int64_t lo = d > m ? d - m : 0, hi = d < n ? d : n;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(B + (d - mid - 1)) < __ldg(A + mid)) hi = mid; else lo = mid + 1;
+    }
+    corank[k] = lo;
+}
+
+// One record per output range [d_k, d_k+1): tile elements each (the last
+// fewer), never packed.
+__global__ void __launch_bounds__(256)
+diagonal_plan_kernel(int64_t n, int64_t m, int64_t tile, int64_t cuts, const int64_t* __restrict__ corank,
+                     TileDesc* __restrict__ desc) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cuts) return;
+    const int64_t d0 = k * tile, d1 = (k + 1) * tile < n + m ? (k + 1) * tile : n + m;
+    const int64_t i0 = __ldg(corank + k), i1 = __ldg(corank + k + 1);
+    TileDesc d{};
+    d.a0 = i0; d.b0 = d0 - i0; d.c0 = d0;
+    d.nA = (int32_t)(i1 - i0); d.nB = (int32_t)((d1 - i1) - (d0 - i0));
+    d.first = 1;
+    desc[k] = d;
+}
+
+// ---------------------------------------------------------------------------
 // Steps 3-4 without the planning pass: one CTA per subproblem (used by the
 // allocation-free entry point, whose scratch holds only the cross ranks)
 // ---------------------------------------------------------------------------
@@ -325,7 +364,7 @@ constexpr int64_t kFusedMaxCap = 17 * 128;
 
 static bool fused_applies(int64_t p, int64_t cap, const tm_config* cfg) {
     if (p > kFusedMaxBlocks || cap > kFusedMaxCap) return false;
-    if (cfg && (cfg->unfused || (cfg->threads && cfg->threads != 128) || cfg->stages || cfg->grid ||
+    if (cfg && (cfg->unfused || cfg->partition || (cfg->threads && cfg->threads != 128) || cfg->stages || cfg->grid ||
                 (cfg->split && cfg->split != TM_SPLIT_DIAGONAL) || cfg->wait_ms || cfg->test_drop_tile))
         return false;
     int dev = 0, coop = 0;
@@ -347,6 +386,20 @@ static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t*
     if (cap > kMaxTileElems) return TM_ERR_UNSUPPORTED;
     const K* A = static_cast<const K*>(a_keys);
     const K* B = static_cast<const K*>(b_keys);
+    if (cfg && cfg->partition == TM_PARTITION_DIAGONALS) {   // ablation: equal output ranges
+        if (cfg->p > 0) return TM_ERR_UNSUPPORTED;            // the cut count follows the tile
+        const int64_t tile = (cfg->tile > 0) ? cfg->tile : kDefaultTile;
+        const int64_t cuts = ceil_div64(n + m, tile);          // == p, the workspace's sizing
+        if (tile > kMaxTileElems || cuts + 1 > 0x7fffffffLL * 256) return TM_ERR_UNSUPPORTED;
+        diagonal_corank_kernel<K><<<(unsigned)((cuts + 1 + 255) / 256), 256, 0, s>>>(A, n, B, m, tile, cuts,
+                                                                                    w.xbar);
+        diagonal_plan_kernel<<<(unsigned)((cuts + 255) / 256), 256, 0, s>>>(n, m, tile, cuts, w.xbar, w.tiles);
+        if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_failed(e);
+        return merge_tiles_dispatch(kt, a_keys, a_vals, n, b_keys, b_vals, m, w.tiles, cuts, (int)tile,
+                                    c_keys, c_vals, w.control, cfg, s);
+    } else if (cfg && cfg->partition != TM_PARTITION_BLOCKS) {
+        return TM_ERR_UNSUPPORTED;
+    }
     if (fused_applies(p, cap, cfg)) {
         EngineArgs a{};
         a.desc = w.tiles;

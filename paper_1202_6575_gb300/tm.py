@@ -37,7 +37,8 @@ class TmConfig(ctypes.Structure):
     """struct tm_config of include/tm.h (0 = default in every field)."""
     _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
-                ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("unfused", ctypes.c_int32)]
+                ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("unfused", ctypes.c_int32),
+                ("partition", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
@@ -314,7 +315,7 @@ def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream
 # ---------------------------------------------------------------------------
 
 def _cfg_dict(c: TmConfig) -> dict:
-    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_}
+    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_ if f != "reserved"}
 
 
 def tm_merge_batched_workspace_size(num_pairs: int, total_a: int, total_b: int, cfg=None) -> int:

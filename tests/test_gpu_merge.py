@@ -171,6 +171,16 @@ def test_keys_only_merge(kt, n, m, cfg):
     assert first_mismatch(to_np(C, kt), K) is None
 
 
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+@pytest.mark.parametrize("n,m,tile", [(0, 5, 64), (7, 0, 64), (1, 1, 64), (5000, 3001, 256),
+                                      (100003, 77777, 2048), (1 << 16, 3, 1000), (3, 1 << 16, 4096)])
+def test_equal_output_partition_ablation(kt, n, m, tile):
+    """partition = TM_PARTITION_DIAGONALS (equal output ranges, the ablation
+    against the paper's blocks) gives the same merge."""
+    A, Av, B, Bv = W.small_merge(n, m, kt, seed=n + 3 * m + tile, alphabet=40)
+    gpu_merge_check(kt, A, Av, B, Bv, cfg={"tile": tile, "partition": 1})
+
+
 def test_fused_launch_in_cuda_graph_replayed():
     A, Av, B, Bv = W.small_merge(60000, 45001, "u32", seed=11, alphabet=1000)
     d = [t.to(DEV) for t in (A, Av, B, Bv)]
