@@ -9,9 +9,34 @@
 
 namespace pmerge {
 
+// Resident CTAs of `bytes` dynamic shared memory on one SM (1 KB reserved per CTA).
+inline int ctas_by_smem(uint32_t bytes) {
+    int dev = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return 0;
+    return per_sm / (int)(bytes + 1024);
+}
+
+// Diagonal split: the consumers hold VT * T outputs, usually more than the
+// largest record.  Staging that many lets two neighbouring records of about
+// half a tile pack into one tile far more often (their sum exceeds the
+// largest single record about half the time), as long as the larger stages
+// keep the same number of CTAs per SM.
+template <typename K, int LOG_T, int S_IN, int S_OUT, int VT>
+int packing_cap(int cap) {
+    const int full = VT << LOG_T;
+    if (cap >= full) return cap;
+    const uint32_t now = make_engine_layout(cap, sizeof(K), 1 << LOG_T, S_IN, S_OUT).total;
+    const uint32_t more = make_engine_layout(full, sizeof(K), 1 << LOG_T, S_IN, S_OUT).total;
+    const int c0 = ctas_by_smem(now);
+    return (c0 > 0 && ctas_by_smem(more) >= c0) ? full : cap;
+}
+
 template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT>
 tm_status launch_engine_s(const EngineArgs& a_in, const tm_config* cfg, cudaStream_t s) {
     EngineArgs a = a_in;
+    if constexpr (SPLIT == kSplitDiagonal) a.cap = packing_cap<K, LOG_T, S_IN, S_OUT, VT>(a.cap);
     a.lay = make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, S_IN, S_OUT);
     a.wait_ns = (cfg && cfg->wait_ms > 0) ? (uint64_t)cfg->wait_ms * 1000000ull : kWaitLimitNs;
     a.drop_fill = (cfg && cfg->test_drop_tile > 0) ? cfg->test_drop_tile - 1 : -1;
