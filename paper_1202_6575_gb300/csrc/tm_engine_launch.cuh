@@ -173,6 +173,10 @@ tm_status launch_fused_vt(const EngineArgs& a_in, cudaStream_t s) {
     lc.attrs = attr;
     lc.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&lc, kern, a);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {   // fewer SMs free than the occupancy says:
+        cudaGetLastError();                           // the caller takes the separate launches
+        return TM_ERR_UNSUPPORTED;
+    }
     return e == cudaSuccess ? TM_OK : cuda_failed(e);
 }
 
