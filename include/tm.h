@@ -311,7 +311,10 @@ TM_API int tm_autotune_clear(void);
  * begin and end into a CUDA graph (thread-local capture mode); replay it
  * with tm_graph_launch on any stream.  The replay reuses the pointers and
  * sizes of the captured calls.  tm_graph_end returns TM_ERR_CUDA if the
- * capture failed (e.g. a call synchronised the stream). */
+ * capture failed (e.g. a call synchronised the stream, or a graph was
+ * destroyed on this thread meanwhile).  Make each kind of call once
+ * outside a capture first: the first call of a kernel configuration sets
+ * its shared-memory limit, which a capture should not have to do. */
 typedef struct tm_graph tm_graph;
 TM_API tm_status tm_graph_capture_begin(tm_stream_t stream);
 TM_API tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out);
