@@ -201,7 +201,7 @@ __device__ __forceinline__ bool locate(const PairSet& ps, const PairBases& pb, i
         p = (__ldg(pb.search_base + k + 1) - __ldg(pb.search_base + k)) / 2;
     } else {
         p = ps.p_uniform;
-        k = t / (2 * p);
+        k = div_nonneg<int64_t>(t, 2 * p);
         if (k >= ps.num_pairs) return false;
         local = t - k * 2 * p;
     }
