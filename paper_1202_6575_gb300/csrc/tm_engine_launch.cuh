@@ -119,6 +119,7 @@ template <typename K, int VT>
 tm_status launch_fused_vt(const EngineArgs& a_in, cudaStream_t s) {
     constexpr int LOG_T = 7;
     EngineArgs a = a_in;
+    a.cap = VT << LOG_T;                           // stage up to the consumers' capacity: records pack
     a.lay = make_engine_layout(a.cap, sizeof(K), 1 << LOG_T, 4, 0);
     a.wait_ns = kWaitLimitNs;
     a.drop_fill = -1;
