@@ -21,6 +21,13 @@
 
 namespace pmerge {
 
+// TM_OK, or TM_ERR_CUDA with the pending launch error recorded for
+// tm_last_cuda_error.
+static tm_status launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
+}
+
 // A set of pairs: either CSR offsets (pair k merges A[a_off[k]..a_off[k+1])
 // with B[b_off[k]..b_off[k+1]) into C from a_off[k] + b_off[k]), or uniform
 // runs of one array (pair k merges the sorted runs [2k*run, (2k+1)*run) and
@@ -388,14 +395,14 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
     } else {
         threads = 2 * ps.p_uniform * ps.num_pairs;
     }
-    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
     const int64_t grid = (threads + 255) / 256;
     if (grid > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     if (grid > 0) {
         batched_search_kernel<K><<<(unsigned)grid, 256, 0, s>>>(ps, pb, A, B, threads, w.xbar, w.ybar);
         batched_plan_kernel<<<(unsigned)grid, 256, 0, s>>>(ps, pb, threads, w.xbar, w.ybar, w.tiles);
     }
-    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
     EngineArgs a{};
     a.desc = w.tiles;
     a.n_items = known_items;                       // -1 in CSR mode: read from the device
@@ -418,7 +425,7 @@ static tm_status batched_typed(int64_t pairs, const int64_t* a_off, const void* 
                                const tm_config* cfg, cudaStream_t s) {
     const int64_t tile = tile_of(cfg);
     BatchedWs w = batched_ws_layout(ws, pairs, total_a + total_b, tile);
-    if (cudaMemsetAsync(w.control, 0, 16, s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(w.control, 0, 16, s); e_ != cudaSuccess) return cuda_failed(e_);
     if (pairs == 0 || total_a + total_b == 0) return TM_OK;
     PairSet ps{};
     ps.num_pairs = pairs; ps.a_off = a_off; ps.b_off = b_off;
@@ -582,7 +589,7 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
                             void* ws, const tm_config* cfg, cudaStream_t s) {
     const int64_t tile = tile_of(cfg);
     BatchedWs w = sort_ws_layout(ws, n, tile);
-    if (cudaMemsetAsync(w.control, 0, 16, s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(w.control, 0, 16, s); e_ != cudaSuccess) return cuda_failed(e_);
     if (n <= 1) return TM_OK;
     K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
     uint32_t* bufv[2] = {vals, tmp_vals};
@@ -594,7 +601,7 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
     const int64_t runs = (n + kSortRun - 1) / kSortRun;
     if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     run_sort_kernel<K><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
-    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
     for (int64_t run = kSortRun; run < n; run *= 2) {
         int64_t items = 0;
         const PairSet ps = sort_round(n, run, tile, &items);
@@ -741,7 +748,11 @@ template <typename Run>
 tm_status tune(int op, tm_key_type kt, int64_t total, size_t ws_have, size_t (*ws_need)(const tm_config*),
                Run run, tm_config* best_out, cudaStream_t s) {
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e = cudaEventCreate(&e0); e != cudaSuccess) return cuda_failed(e);
+    if (const cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_failed(e);
+    }
     float best_ms = -1.f;
     tm_config best{};
     for (const tm_config& c : tune_candidates()) {
@@ -808,9 +819,10 @@ tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t*
     // every trial sorts a fresh copy of the source; the copy is outside the
     // timed sort only in the sense that it is the same for every candidate
     auto run = [&](const tm_config* c) -> tm_status {
-        if (cudaMemcpyAsync(keys, src_keys, (size_t)n * E, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(vals, src_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return TM_ERR_CUDA;
+        cudaError_t e = cudaMemcpyAsync(keys, src_keys, (size_t)n * E, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && vals)                 // keys-only sort: no payloads to copy
+            e = cudaMemcpyAsync(vals, src_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_failed(e);
         return tm_merge_sort(kt, keys, vals, n, tmp_keys, tmp_vals, workspace, workspace_bytes, c, stream);
     };
     return tune(2, kt, n, workspace_bytes, sort_ws_need, run, best, s);
@@ -834,19 +846,22 @@ struct tm_graph {
 
 tm_status tm_graph_capture_begin(tm_stream_t stream) {
     if (!stream) return TM_ERR_INVALID;              // the legacy stream cannot be captured
-    return cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal) ==
-                   cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    const cudaError_t e = cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream),
+                                                 cudaStreamCaptureModeThreadLocal);
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
 }
 
 tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out) {
     if (!stream || !out) return TM_ERR_INVALID;
     *out = nullptr;
     cudaGraph_t g = nullptr;
-    if (cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &g) != cudaSuccess || !g) return TM_ERR_CUDA;
+    if (const cudaError_t err = cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &g);
+        err != cudaSuccess || !g)
+        return cuda_failed(err != cudaSuccess ? err : cudaErrorStreamCaptureInvalidated);
     cudaGraphExec_t e = nullptr;
-    if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+    if (const cudaError_t err = cudaGraphInstantiate(&e, g, 0); err != cudaSuccess) {
         cudaGraphDestroy(g);
-        return TM_ERR_CUDA;
+        return cuda_failed(err);
     }
     tm_graph* h = new (std::nothrow) tm_graph{g, e};
     if (!h) {
@@ -860,7 +875,8 @@ tm_status tm_graph_capture_end(tm_stream_t stream, tm_graph** out) {
 
 tm_status tm_graph_launch(tm_graph* g, tm_stream_t stream) {
     if (!g) return TM_ERR_INVALID;
-    return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    const cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
 }
 
 void tm_graph_destroy(tm_graph* g) {

@@ -33,6 +33,13 @@
 
 namespace pmerge {
 
+// TM_OK, or TM_ERR_CUDA with the pending launch error recorded for
+// tm_last_cuda_error.
+static tm_status launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
+}
+
 struct CdfHeader {
     int32_t S, H;
     float eps_frac;
@@ -519,12 +526,12 @@ tm_status tm_cdf_init(void* model, int segments, int hidden, const float* base_k
     uint8_t* b = static_cast<uint8_t*>(model);
     cdf_knots_kernel<<<(segments + 256) / 256, 256, 0, s>>>(base_keys, n, segments, reinterpret_cast<float*>(b + L.K),
                                                           reinterpret_cast<int64_t*>(b + L.R0));
-    if (cudaMemsetAsync(b + L.eps_seg, 0, (size_t)segments * sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(b + L.eps_seg, 0, (size_t)segments * sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
     cdf_init_kernel<<<1, 256, 0, s>>>(reinterpret_cast<CdfHeader*>(b), segments, hidden, n,
                                       reinterpret_cast<float*>(b + L.params), init_params,
                                       reinterpret_cast<float*>(b + L.m), reinterpret_cast<float*>(b + L.v),
                                       reinterpret_cast<float*>(b + L.grad));
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 tm_status tm_cdf_grad(void* model, int segments, int hidden, const float* q, const int64_t* labels, int64_t count,
@@ -538,15 +545,15 @@ tm_status tm_cdf_grad(void* model, int segments, int hidden, const float* q, con
     CdfHeader* hdr = static_cast<CdfHeader*>(model);
     CdfView v = cdf_view(model, segments, hidden);
     float* g = reinterpret_cast<float*>(static_cast<uint8_t*>(model) + L.grad);
-    if (cudaMemsetAsync(g, 0, P * sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
-    if (cudaMemsetAsync(&hdr->loss, 0, sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(g, 0, P * sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
+    if (const cudaError_t e_ = cudaMemsetAsync(&hdr->loss, 0, sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
     const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
     cdf_grad_kernel<<<(unsigned)blocks, 256, 2 * P * sizeof(float), s>>>(v, q, labels, count, g, hdr);
-    if (cudaMemcpyAsync(grad_out, g, P * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(loss_out, &hdr->loss, sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(g, 0, P * sizeof(float), s) != cudaSuccess)
-        return TM_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    if (const tm_status st = launch_status(); st != TM_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(grad_out, g, P * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss_out, &hdr->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, P * sizeof(float), s);
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
 }
 
 tm_status tm_cdf_train(void* model, int segments, int hidden, const float* q, const int64_t* labels, int64_t count,
@@ -562,14 +569,14 @@ tm_status tm_cdf_train(void* model, int segments, int hidden, const float* q, co
     CdfView v = cdf_view(model, segments, hidden);
     float* g = reinterpret_cast<float*>(b + L.grad);
     const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
-    if (cudaMemsetAsync(g, 0, P * sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(g, 0, P * sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
     for (int it = 0; it < steps; ++it) {
-        if (cudaMemsetAsync(&hdr->loss, 0, sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
+        if (const cudaError_t e_ = cudaMemsetAsync(&hdr->loss, 0, sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
         cdf_grad_kernel<<<(unsigned)blocks, 256, 2 * P * sizeof(float), s>>>(v, q, labels, count, g, hdr);
         cdf_adam_kernel<<<1, 288, 0, s>>>(hdr, reinterpret_cast<float*>(b + L.params), reinterpret_cast<float*>(b + L.m),
                                           reinterpret_cast<float*>(b + L.v), g, P, lr);
     }
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 tm_status tm_cdf_predict(const void* model, int segments, int hidden, const float* q, int64_t count, float* pred,
@@ -582,7 +589,7 @@ tm_status tm_cdf_predict(const void* model, int segments, int hidden, const floa
     CdfView v = cdf_view(const_cast<void*>(model), segments, hidden);
     cdf_predict_kernel<<<(unsigned)((count + 255) / 256), 256, P * sizeof(float), s>>>(
         v, q, count, pred, nullptr, nullptr, const_cast<CdfHeader*>(v.hdr));
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 tm_status tm_cdf_calibrate(void* model, int segments, int hidden, const float* q, const int64_t* labels,
@@ -593,11 +600,11 @@ tm_status tm_cdf_calibrate(void* model, int segments, int hidden, const float* q
     const int P = 4 * hidden + 1;
     CdfHeader* hdr = static_cast<CdfHeader*>(model);
     CdfView v = cdf_view(model, segments, hidden);
-    if (cudaMemsetAsync(&hdr->eps_frac, 0, sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
-    if (cudaMemsetAsync(v.eps_seg, 0, (size_t)segments * sizeof(float), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(&hdr->eps_frac, 0, sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
+    if (const cudaError_t e_ = cudaMemsetAsync(v.eps_seg, 0, (size_t)segments * sizeof(float), s); e_ != cudaSuccess) return cuda_failed(e_);
     cdf_predict_kernel<<<(unsigned)((count + 255) / 256), 256, P * sizeof(float), s>>>(
         v, q, count, nullptr, nullptr, labels, hdr);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const float* a_keys, int64_t n,
@@ -611,7 +618,7 @@ tm_status tm_cross_ranks_learned(void* model, int segments, int hidden, const fl
     const int64_t threads = 2 * p + 2 + segments;
     learned_cross_rank_kernel<<<(unsigned)((threads + 255) / 256), 256, (size_t)hidden * sizeof(float4), s>>>(
         v, static_cast<CdfHeader*>(model), a_keys, n, b_keys, m, p, xbar, ybar, flags & TM_LEARNED_ADVANCE);
-    if (cudaGetLastError() != cudaSuccess) return TM_ERR_CUDA;
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
 
     return TM_OK;
 }
@@ -632,7 +639,7 @@ tm_status tm_merge_learned(void* model, int segments, int hidden,
     int64_t* xbar = reinterpret_cast<int64_t*>(w + kStatusBytes);
     int64_t* ybar = reinterpret_cast<int64_t*>(w + kStatusBytes + align_up((size_t)(p + 1) * 8, 256));
     void* tiles = w + kStatusBytes + 2 * align_up((size_t)(p + 1) * 8, 256);
-    if (cudaMemsetAsync(w, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e_ = cudaMemsetAsync(w, 0, sizeof(int32_t), s); e_ != cudaSuccess) return cuda_failed(e_);
     tm_status st = tm_cross_ranks_learned(model, segments, hidden, a_keys, n, b_keys, m, p, xbar, ybar, flags,
                                           stream);
     if (st != TM_OK) return st;

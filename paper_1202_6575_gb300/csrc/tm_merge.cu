@@ -10,6 +10,13 @@
 
 namespace pmerge {
 
+// TM_OK, or TM_ERR_CUDA with the pending launch error recorded for
+// tm_last_cuda_error.
+static tm_status launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TM_OK : cuda_failed(e);
+}
+
 static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
 void record_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
 static cudaError_t last_cuda_error() { return g_last_cuda_error; }
@@ -251,7 +258,7 @@ static tm_status launch_tile_merge(const K* A, const uint32_t* Av, int64_t n,
     if (!ensure_smem_limit(tile_merge_kernel<K>, g.lay.bytes)) return TM_ERR_UNSUPPORTED;
     if (2 * p > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     tile_merge_kernel<K><<<(unsigned)(2 * p), T, g.lay.bytes, s>>>(g);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 template <typename K>
@@ -261,7 +268,7 @@ static tm_status launch_cross_ranks(const K* A, int64_t n, const K* B, int64_t m
     int64_t blocks = ceil_div64(threads, 256);
     if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     cross_rank_kernel<K><<<(unsigned)blocks, 256, 0, s>>>(A, n, B, m, p, xbar, ybar);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 // ---------------------------------------------------------------------------
@@ -324,7 +331,7 @@ static tm_status launch_plan_single(int64_t n, int64_t m, int64_t p, const int64
     int64_t blocks = (2 * p + 255) / 256;
     if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     plan_single_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, m, p, xbar, ybar, desc);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 // Largest subproblem of the single merge: one A-block piece plus one B-block
@@ -449,9 +456,10 @@ const char* tm_last_cuda_error(void) { return cudaGetErrorName(last_cuda_error()
 tm_status tm_read_status(const void* status, tm_stream_t stream) {
     if (!status) return TM_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e = cudaStreamSynchronize(s); e != cudaSuccess) return cuda_failed(e);
     int32_t h = 0;
-    if (cudaMemcpy(&h, status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return TM_ERR_CUDA;
+    if (const cudaError_t e = cudaMemcpy(&h, status, sizeof(h), cudaMemcpyDeviceToHost); e != cudaSuccess)
+        return cuda_failed(e);
     return static_cast<tm_status>(h);
 }
 
@@ -556,7 +564,7 @@ tm_status tm_subproblems(int64_t n, int64_t m, int64_t p, const int64_t* xbar,
     if (blocks > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     subproblem_table_kernel<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         n, m, p, xbar, ybar, table);
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 tm_status tm_rank_search(tm_key_type kt, int kind, const void* q, int64_t count,
@@ -575,7 +583,7 @@ tm_status tm_rank_search(tm_key_type kt, int kind, const void* q, int64_t count,
         case TM_KEY_U64: rank_search_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>((const uint64_t*)q, count, (const uint64_t*)x_keys, len, kind, out); break;
         case TM_KEY_F32: rank_search_kernel<float><<<(unsigned)blocks, 256, 0, s>>>((const float*)q, count, (const float*)x_keys, len, kind, out); break;
     }
-    return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ERR_CUDA;
+    return launch_status();
 }
 
 }  // extern "C"
@@ -603,7 +611,10 @@ static int64_t* noalloc_ranks_ptr() {
     std::lock_guard<std::mutex> lock(mu);
     if (!addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_ranks) != cudaSuccess) return nullptr;
+        if (const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ranks); e != cudaSuccess) {
+            record_cuda_error(e);
+            return nullptr;
+        }
         addr[dev] = static_cast<int64_t*>(p);
     }
     return addr[dev];
@@ -618,7 +629,10 @@ static tm_status merge_noalloc_typed(const void* a_keys, const uint32_t* a_vals,
     if (!ranks) return TM_ERR_CUDA;
     int64_t* xbar = ranks;
     int64_t* ybar = ranks + (kNoAllocMaxBlocks + 1);
-    if (status && cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return TM_ERR_CUDA;
+    if (status) {
+        if (const cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s); e != cudaSuccess)
+            return cuda_failed(e);
+    }
     if (n + m == 0) return TM_OK;
     const K* A = static_cast<const K*>(a_keys);
     const K* B = static_cast<const K*>(b_keys);
