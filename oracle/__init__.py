@@ -34,6 +34,10 @@ _SRC = os.path.join(_HERE, "tm_oracle.c")
 _SRC_PAR = os.path.join(_HERE, "paper_parallel.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# A prebuilt copy of the oracle library to load instead of building this one:
+# tests/test_oracle_mutants.py points it at copies with one planted mistake
+# each, to show that the pins catch every such mistake.
+_LIB_OVERRIDE = os.environ.get("TM_ORACLE_LIB")
 
 _KEY_SUFFIX = {
     np.dtype(np.uint32): "u32",
@@ -67,8 +71,11 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build()
-        _lib = ctypes.CDLL(_LIB_PATH)
+        if _LIB_OVERRIDE:
+            _lib = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
         i64, p = ctypes.c_int64, ctypes.c_void_p
         _lib.orc_block_start.restype = i64
         _lib.orc_block_start.argtypes = [i64, i64, i64]
@@ -258,3 +265,16 @@ def merge_sort(keys, vals, run: int = 1):
     getattr(_load(), f"orc_merge_sort_{_suffix(k)}")(
         _ptr(k), _ptr(v), len(k), run, _ptr(tk), _ptr(tv))
     return k, v
+
+
+# The same for the learned-model oracle: a planted copy of cdf.py replaces
+# the real one as ``oracle.cdf`` when TM_ORACLE_CDF names it.
+_CDF_OVERRIDE = os.environ.get("TM_ORACLE_CDF")
+if _CDF_OVERRIDE:
+    import importlib.util
+    import sys
+
+    _spec = importlib.util.spec_from_file_location(__name__ + ".cdf", _CDF_OVERRIDE)
+    cdf = importlib.util.module_from_spec(_spec)
+    sys.modules[_spec.name] = cdf
+    _spec.loader.exec_module(cdf)

@@ -124,3 +124,56 @@ def test_training_reduces_loss_and_bounds_error():
     fw = cdf.forward(P, q, K, R)
     # every label lies within eps segment units of the prediction
     assert np.all(np.abs(fw["pred"] - L) <= eps * fw["scale"] + 1e-6)
+
+
+def test_pla_exact_outside_the_base():
+    # Below X[0] the exact rank_high is 0 and from X[N-1] up it is N (the
+    # definition of rank_high, Section 2); the piecewise-linear part must
+    # give exactly these, whatever the knots.
+    rng = np.random.default_rng(5)
+    X, _, _, K, R = base_and_labels(rng)
+    q = np.array([X[0] - 3.0, X[0] - 1e-3, X[-1], X[-1] + 1e-3, X[-1] + 50.0], dtype=np.float32)
+    fw = cdf.forward(cdf_zero(), q, K, R)
+    exact = [oracle.rank_high(v, X) for v in q]
+    assert exact == [0, 0, len(X), len(X), len(X)]
+    assert fw["pla"].tolist() == [float(e) for e in exact]
+    assert np.all((fw["t"] >= 0.0) & (fw["t"] <= 1.0))
+
+
+def test_segment_feature_is_the_segment_midpoint():
+    # f1 places segment s at the midpoint of the s-th of S equal parts of
+    # [-1, 1]; f0 maps the position in the segment onto [-1, 1].
+    rng = np.random.default_rng(6)
+    X, _, _, K, R = base_and_labels(rng, S=16)
+    S = len(K) - 1
+    q = np.sort(rng.uniform(float(X[0]), float(X[-1]), size=4000)).astype(np.float32)
+    s, t, f0, f1 = cdf.features(q, K)
+    mids = np.linspace(-1.0, 1.0, 2 * S + 1)[1::2]
+    assert len(np.unique(s)) > S // 2
+    assert np.allclose(f1, mids[s], atol=1e-15)
+    assert np.allclose(f0, -1.0 + 2.0 * t, atol=1e-15)
+    assert np.all(np.abs(f0) <= 1.0)
+
+
+def test_loss_is_half_squared_error_of_the_predicted_rank():
+    # Independent of the target's algebra: with pred the model's rank
+    # estimate, the loss is the mean of ((pred - L) / scale)^2 / 2.
+    rng = np.random.default_rng(7)
+    X, q, L, K, R = base_and_labels(rng)
+    P = params_random(rng)
+    loss, _, fw, _ = cdf.loss_and_grads(P, q, L, K, R)
+    err = (fw["pred"] - L) / fw["scale"]
+    assert np.isclose(loss, 0.5 * np.mean(err * err), rtol=1e-12)
+
+
+def test_error_bound_covers_underestimates():
+    # A model that predicts below every label: the bound is the largest
+    # distance, not the largest signed residual.
+    rng = np.random.default_rng(8)
+    X, q, L, K, R = base_and_labels(rng)
+    P = params_random(rng)
+    P["b2"] = np.float64(-50.0)
+    fw = cdf.forward(P, q, K, R)
+    assert np.all(fw["pred"] < L)
+    eps = cdf.error_bound_frac(P, q, L, K, R)
+    assert np.isclose(eps, np.max(np.abs(fw["pred"] - L) / fw["scale"]), rtol=1e-12)
