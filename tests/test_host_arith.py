@@ -1,0 +1,114 @@
+"""The library's block arithmetic of Section 2 (block starts, block of an
+index, first block starting at or after an index, and the division with its
+32-bit fast path), compiled for the host from the same header the kernels
+use, against the oracle and exact integer arithmetic: exhaustively on small
+sizes and at sizes up to 2^62 that no GPU test can allocate.  No GPU is
+used (nvcc cross-compiles the harness; only host code runs).
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HARNESS = os.path.join(ROOT, "tests", "host", "block_arith.cu")
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    cc = _nvcc()
+    if cc is None:
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("host_arith") / "libblock_arith.so")
+    subprocess.check_call([cc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                           "-Xcompiler", "-fPIC", "-shared",
+                           "-I" + os.path.join(ROOT, "include"),
+                           "-I" + os.path.join(ROOT, "paper_1202_6575_gb300", "csrc"),
+                           HARNESS, "-o", out])
+    L = ctypes.CDLL(out)
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    for name, t in (("h_div_nonneg64", i64), ("h_block_start64", i64), ("h_block_of64", i64),
+                    ("h_first_block64", i64)):
+        f = getattr(L, name)
+        f.restype = t
+        f.argtypes = [t] * (2 if "div" in name else 3)
+    for name in ("h_div_nonneg32", "h_block_start32"):
+        f = getattr(L, name)
+        f.restype = i32
+        f.argtypes = [i32] * (2 if "div" in name else 3)
+    return L
+
+
+def first_block_brute(length, p, k):
+    """Smallest j with block start y_j >= k, by bisection over the oracle's
+    (non-decreasing) block starts; for k = len with len < p the first empty
+    block, j = len (its start is len)."""
+    lo, hi = 0, p
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if oracle.block_start(length, p, mid) >= k:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
+def test_small_sizes_exhaustive_against_the_oracle(lib):
+    for length in range(0, 41):
+        for p in range(1, 14):
+            for i in range(p + 1):
+                assert lib.h_block_start64(length, p, i) == oracle.block_start(length, p, i)
+                assert lib.h_block_start32(length, p, i) == oracle.block_start(length, p, i)
+            for k in range(length + 1):
+                assert lib.h_block_of64(length, p, k) == oracle.block_of(length, p, k), (length, p, k)
+                assert lib.h_first_block64(length, p, k) == first_block_brute(length, p, k), (length, p, k)
+
+
+def test_large_sizes_against_exact_integers(lib):
+    rng = np.random.default_rng(11)
+    cases = []
+    for e_len in (31, 32, 33, 40, 50, 62):
+        for _ in range(60):
+            length = int(rng.integers(1 << (e_len - 1), (1 << e_len) + 1))
+            p = int(rng.choice([1, 2, 3, 1023, 1024, 65537, (1 << 31) - 1, 1 << 31, (1 << 32) + 3]))
+            p = max(1, min(p, length + 5))
+            cases.append((length, p))
+    cases += [((1 << 62) - 1, (1 << 31) - 1), ((1 << 32) - 1, 1 << 16), (1 << 32, 1 << 16),
+              ((1 << 32) + 1, 3), (5, 1 << 40)]
+    for length, p in cases:
+        q, r = divmod(length, p)
+        for i in sorted(i for i in {0, 1, r - 1, r, r + 1, p // 2, p - 1, p} if 0 <= i <= p):
+            exact = i * (q + 1) if i < r else i * q + r       # first r blocks hold q + 1 elements
+            assert lib.h_block_start64(length, p, i) == exact, (length, p, i)
+            if i < p and exact < length:
+                assert lib.h_block_of64(length, p, exact) == i
+                nxt = i * (q + 1) + q + 1 if i < r else (i + 1) * q + r
+                assert lib.h_block_of64(length, p, nxt - 1) == i
+                assert lib.h_first_block64(length, p, exact) == i
+                if nxt - exact > 1:
+                    assert lib.h_first_block64(length, p, exact + 1) == i + 1
+        assert lib.h_block_of64(length, p, length) == p
+        assert lib.h_first_block64(length, p, length) == (length if length < p else p)
+
+
+def test_division_fast_path_boundaries(lib):
+    vals = [0, 1, 2, 3, 7, (1 << 31) - 1, 1 << 31, (1 << 32) - 2, (1 << 32) - 1, 1 << 32, (1 << 32) + 1,
+            (1 << 40) + 12345, (1 << 62) - 1, (1 << 63) - 1]
+    for a in vals:
+        for b in vals[1:]:
+            assert lib.h_div_nonneg64(a, b) == a // b, (a, b)
+    for a in (0, 1, 5, (1 << 31) - 1):
+        for b in (1, 2, 3, (1 << 31) - 1):
+            assert lib.h_div_nonneg32(a, b) == a // b
