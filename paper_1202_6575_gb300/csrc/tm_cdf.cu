@@ -628,8 +628,11 @@ tm_status tm_merge_learned(void* model, int segments, int hidden,
                            const float* b_keys, const uint32_t* b_vals, int64_t m,
                            float* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
                            const tm_config* cfg, int flags, tm_stream_t stream) {
-    if (n < 1 || m < 0) return TM_ERR_INVALID;
-    if (!aligned(c_keys, 4) || !payloads_ok(n, a_vals, m, b_vals, c_vals)) return TM_ERR_INVALID;
+    // every argument rule of the calls below, checked before anything is issued
+    if (!model_ok(model, segments, hidden) || n < 1 || m < 0) return TM_ERR_INVALID;
+    if (!aligned(a_keys, 4) || (m > 0 && !aligned(b_keys, 4)) || !aligned(c_keys, 4) ||
+        !payloads_ok(n, a_vals, m, b_vals, c_vals))
+        return TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p))
         return TM_ERR_WORKSPACE;

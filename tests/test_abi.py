@@ -78,3 +78,82 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     # the allocation-free entry point has no keys-only form
     assert lib.tm_merge_noalloc(0, P(16), None, 3, P(32), None, 1, P(64), None, None, None, None) == \
         tm.TM_ERR_UNSUPPORTED
+
+
+def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
+    """Every entry point's documented argument rules, on the host: each case
+    returns its code before anything reaches the GPU (there is none here)."""
+    P = ctypes.c_void_p
+    INV, UNS, WS = tm.TM_ERR_INVALID, tm.TM_ERR_UNSUPPORTED, tm.TM_ERR_WORKSPACE
+    off, k8, v4, ws = P(64), P(128), P(256), P(512)
+
+    def batched(fn, pairs=2, aoff=off, ak=k8, av=v4, na=10, boff=off, bk=k8, bv=v4, nb=6, ck=k8, cv=v4,
+                w=ws, wb=1 << 30, kt=2, last=None):
+        args = [kt, pairs, aoff, ak, av, na, boff, bk, bv, nb, ck, cv, w, wb, last, None]
+        return getattr(lib, fn)(*args)
+
+    for fn in ("tm_merge_batched", "tm_autotune_batched"):
+        assert batched(fn, pairs=-1) == INV
+        assert batched(fn, na=-1) == INV
+        assert batched(fn, kt=9) == UNS
+        assert batched(fn, aoff=P(68)) == INV                    # offsets are int64
+        assert batched(fn, bk=P(132)) == INV                     # u64 keys need 8-byte alignment
+        assert batched(fn, av=None) == INV                       # payloads: all or none
+        assert batched(fn, cv=None) == INV
+        assert batched(fn, av=None, bv=None, cv=None, w=None) == WS   # keys only passes, then the workspace
+        assert batched(fn, w=P(520)) == WS                       # workspace not 256-byte aligned
+    assert batched("tm_merge_batched", wb=16) == WS
+    assert lib.tm_merge_batched_workspace_size(-1, 0, 0, None) == 0
+    assert lib.tm_merge_batched_workspace_size(4, 100, 100, None) > 0
+
+    # tm_merge_sort(kt, keys, vals, n, tmp_keys, tmp_vals, ws, bytes, cfg, stream)
+    assert lib.tm_merge_sort(2, k8, v4, -1, k8, v4, ws, 1 << 30, None, None) == INV
+    assert lib.tm_merge_sort(9, k8, v4, 8, k8, v4, ws, 1 << 30, None, None) == UNS
+    assert lib.tm_merge_sort(2, P(132), v4, 8, k8, v4, ws, 1 << 30, None, None) == INV
+    assert lib.tm_merge_sort(2, k8, v4, 8, k8, None, ws, 1 << 30, None, None) == INV
+    assert lib.tm_merge_sort(2, k8, None, 8, k8, None, None, 0, None, None) == WS
+    assert lib.tm_merge_sort(2, k8, v4, 8, k8, v4, ws, 8, None, None) == WS
+    assert lib.tm_merge_sort_workspace_size(-1, None) == 0
+    # tm_autotune_sort(kt, src_k, src_v, n, keys, vals, tmp_k, tmp_v, ws, bytes, best, stream)
+    assert lib.tm_autotune_sort(2, k8, v4, -1, k8, v4, k8, v4, ws, 1 << 30, None, None) == INV
+    assert lib.tm_autotune_sort(9, k8, v4, 8, k8, v4, k8, v4, ws, 1 << 30, None, None) == UNS
+    assert lib.tm_autotune_sort(2, k8, None, 8, k8, v4, k8, v4, ws, 1 << 30, None, None) == INV
+    assert lib.tm_autotune_sort(2, k8, v4, 8, k8, v4, k8, v4, None, 0, None, None) == WS
+
+    # graphs: the legacy stream cannot be captured; NULL handles
+    h = ctypes.c_void_p()
+    assert lib.tm_graph_capture_begin(None) == INV
+    assert lib.tm_graph_capture_end(None, ctypes.byref(h)) == INV
+    assert lib.tm_graph_launch(None, None) == INV
+    lib.tm_graph_destroy(None)
+    assert lib.tm_read_status(None, None) == INV
+
+    # learned model: dimensions, alignment, counts
+    assert lib.tm_cdf_model_bytes(1, 64) == 0 and lib.tm_cdf_model_bytes(4096, 0) == 0
+    assert lib.tm_cdf_model_bytes(4096, 2048) == 0
+    mb = lib.tm_cdf_model_bytes(4096, 64)
+    assert mb > 0 and mb % 256 == 0
+    model, q, lab, out = P(1 << 20), P(4096), P(8192), P(16384)
+    assert lib.tm_cdf_init(P((1 << 20) + 64), 4096, 64, q, 100, q, None) == INV   # model not 256-aligned
+    assert lib.tm_cdf_init(model, 4096, 64, q, 0, q, None) == INV
+    assert lib.tm_cdf_grad(model, 4096, 64, q, lab, 0, out, out, None) == INV
+    assert lib.tm_cdf_grad(model, 4096, 64, q, P(8196), 10, out, out, None) == INV   # labels are int64
+    assert lib.tm_cdf_train(model, 4096, 64, q, lab, 10, -1, 1e-3, None) == INV
+    assert lib.tm_cdf_predict(model, 4096, 64, q, -1, out, None) == INV
+    assert lib.tm_cdf_predict(model, 4096, 64, q, 0, out, None) == tm.TM_OK          # nothing to do
+    assert lib.tm_cdf_calibrate(model, 4096, 64, q, lab, 0, None) == INV
+    # tm_cross_ranks_learned(model, S, H, a, n, b, m, p, xbar, ybar, flags, stream)
+    assert lib.tm_cross_ranks_learned(model, 4096, 64, q, 100, q, 10, 0, out, out, 0, None) == INV
+    assert lib.tm_cross_ranks_learned(model, 4096, 64, q, 0, q, 10, 4, out, out, 0, None) == INV
+    assert lib.tm_cross_ranks_learned(model, 4096, 64, q, 100, q, 10, 4, P(16388), out, 0, None) == INV
+    # tm_merge_learned(model, S, H, a, av, n, b, bv, m, c, cv, ws, bytes, cfg, flags, stream)
+    assert lib.tm_merge_learned(model, 4096, 64, q, v4, 0, q, v4, 10, q, v4, ws, 1 << 30, None, 0, None) == INV
+    assert lib.tm_merge_learned(model, 4096, 64, q, None, 100, q, v4, 10, q, v4, ws, 1 << 30, None, 0,
+                                None) == INV
+    assert lib.tm_merge_learned(model, 1, 64, q, v4, 100, q, v4, 10, q, v4, ws, 1 << 30, None, 0, None) == INV
+    assert lib.tm_merge_learned(model, 4096, 64, P(4098), v4, 100, q, v4, 10, q, v4, ws, 1 << 30, None, 0,
+                                None) == INV
+    assert lib.tm_merge_learned(model, 4096, 64, q, v4, 100, q, v4, 10, q, v4, None, 0, None, 0, None) == WS
+    # the allocation-free merge: lengths, key type, alignment
+    assert lib.tm_merge_noalloc(0, k8, v4, -1, k8, v4, 1, k8, v4, None, None, None) == INV
+    assert lib.tm_merge_noalloc(9, k8, v4, 1, k8, v4, 1, k8, v4, None, None, None) == UNS
