@@ -133,9 +133,12 @@ def test_learned_lsm_merges_exact_and_knots_advance():
         C, Cv, ws = tm.tm_merge_learned(model, A, Av, B, Bv, flags=tm.LEARNED_ADVANCE)
         assert tm.tm_read_status(ws) == 0
         check_merge_equal(C, Cv, A, Av, B, Bv)
-        # the learned Steps 1-2 return exactly the plain cross ranks
+        # the learned Steps 1-2 return exactly the plain cross ranks (xbar
+        # after the 256-byte control block, ybar on the next 256-byte boundary)
         xl = ws[256:256 + 8 * (p + 1)].view(torch.int64)
-        assert torch.equal(xl, xb_plain)
+        y_off = 256 + (8 * (p + 1) + 255) // 256 * 256
+        yl = ws[y_off:y_off + 8 * (p + 1)].view(torch.int64)
+        assert torch.equal(xl, xb_plain) and torch.equal(yl, yb_plain)
         h = model.header()
         assert h["cur"] == 1 - cur and h["N"] == n + m
         # knot ranks now locate the knot keys in the merged base
