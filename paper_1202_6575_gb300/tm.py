@@ -32,6 +32,9 @@ TM_ERR_BOUNDS = 6
 SPLIT_BLOCKS = 1
 SPLIT_DIAGONAL = 2
 
+# Payloads are opaque 32-bit words (int32 tensors; uint32 where torch has it).
+PAYLOAD_DTYPES = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+
 
 class TmConfig(ctypes.Structure):
     """struct tm_config of include/tm.h (0 = default in every field)."""
@@ -155,12 +158,12 @@ def _stream(stream) -> int:
 def _dev(t, name: str, dtypes=None) -> int:
     if t is None:                       # optional array (payloads of a keys-only call)
         return 0
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
-    if not t.is_contiguous():
-        raise ValueError(f"{name} must be contiguous")
     if dtypes is not None and t.dtype not in dtypes:
         raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
     return t.data_ptr() if t.numel() else 0
 
 
@@ -203,8 +206,8 @@ def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, s
     cfgp = _cfg(cfg)
     if workspace is None:
         workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)
-    code = load().tm_merge(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd), _dev(Bv, "Bv"), m,
-                           _dev(C, "C", kd), _dev(Cv, "Cv"), _dev(workspace, "workspace"),
+    code = load().tm_merge(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), n, _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), m,
+                           _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES), _dev(workspace, "workspace"),
                            workspace.numel(), cfgp, _stream(stream))
     _check(code, "tm_merge")
     return C, Cv, workspace
@@ -259,8 +262,8 @@ def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None,
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
     if control is None:
         control = torch.zeros(256, dtype=torch.uint8, device=A.device)
-    code = load().tm_merge_tiles(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd), _dev(Bv, "Bv"), m,
-                                 _dev(tiles, "tiles"), n_tiles, cap, _dev(C, "C", kd), _dev(Cv, "Cv"),
+    code = load().tm_merge_tiles(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), n, _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), m,
+                                 _dev(tiles, "tiles"), n_tiles, cap, _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES),
                                  _dev(control, "control"), _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_tiles")
     return C, Cv, control
@@ -302,8 +305,8 @@ def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream
     n, m = A.numel(), B.numel()
     if C.numel() != n + m or Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m:
         raise ValueError("length mismatch")
-    code = load().tm_merge_noalloc(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av"), n, _dev(B, "B", kd),
-                                   _dev(Bv, "Bv"), m, _dev(C, "C", kd), _dev(Cv, "Cv"),
+    code = load().tm_merge_noalloc(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), n, _dev(B, "B", kd),
+                                   _dev(Bv, "Bv", PAYLOAD_DTYPES), m, _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES),
                                    None if status is None else _dev(status, "status", (torch.int32,)),
                                    _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_noalloc")
@@ -332,9 +335,9 @@ def _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv):
         C = torch.empty(ta + tb, dtype=A.dtype, device=A.device)
     if Cv is None and (Av is not None or Bv is not None):
         Cv = torch.empty(ta + tb, dtype=torch.int32, device=A.device)
-    args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av"), ta,
-            _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv"), tb,
-            _dev(C, "C", kd), _dev(Cv, "Cv"))
+    args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), ta,
+            _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), tb,
+            _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES))
     return args, C, Cv, pairs, ta, tb
 
 
@@ -364,8 +367,8 @@ def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=N
         tmp_vals = torch.empty_like(vals)
     if workspace is None:
         workspace = new_workspace(tm_merge_sort_workspace_size(n, cfg), keys.device)
-    code = load().tm_merge_sort(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals"), n,
-                                _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals"),
+    code = load().tm_merge_sort(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals", PAYLOAD_DTYPES), n,
+                                _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", PAYLOAD_DTYPES),
                                 _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_sort")
     return keys, vals, workspace
@@ -383,9 +386,9 @@ def tm_autotune_batched(kt: str, a_off, A, Av, b_off, B, Bv, C, Cv, workspace, s
 def tm_autotune_sort(kt: str, src_keys, src_vals, keys, vals, tmp_keys, tmp_vals, workspace, stream=None) -> dict:
     kd = TORCH_KEY_DTYPES[kt]
     best = TmConfig()
-    code = load().tm_autotune_sort(_kt(kt), _dev(src_keys, "src_keys", kd), _dev(src_vals, "src_vals"),
-                                   src_keys.numel(), _dev(keys, "keys", kd), _dev(vals, "vals"),
-                                   _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals"),
+    code = load().tm_autotune_sort(_kt(kt), _dev(src_keys, "src_keys", kd), _dev(src_vals, "src_vals", PAYLOAD_DTYPES),
+                                   src_keys.numel(), _dev(keys, "keys", kd), _dev(vals, "vals", PAYLOAD_DTYPES),
+                                   _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", PAYLOAD_DTYPES),
                                    _dev(workspace, "workspace"), workspace.numel(), ctypes.byref(best),
                                    _stream(stream))
     _check(code, "tm_autotune_sort")
@@ -551,8 +554,8 @@ def tm_merge_learned(model: CdfModel, A, Av, B, Bv, C=None, Cv=None, workspace=N
         Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
     if workspace is None:
         workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)
-    _check(load().tm_merge_learned(model._p(), model.S, model.H, _dev(A, "A", (torch.float32,)), _dev(Av, "Av"), n,
-                                   _dev(B, "B", (torch.float32,)), _dev(Bv, "Bv"), m,
-                                   _dev(C, "C", (torch.float32,)), _dev(Cv, "Cv"), _dev(workspace, "workspace"),
+    _check(load().tm_merge_learned(model._p(), model.S, model.H, _dev(A, "A", (torch.float32,)), _dev(Av, "Av", PAYLOAD_DTYPES), n,
+                                   _dev(B, "B", (torch.float32,)), _dev(Bv, "Bv", PAYLOAD_DTYPES), m,
+                                   _dev(C, "C", (torch.float32,)), _dev(Cv, "Cv", PAYLOAD_DTYPES), _dev(workspace, "workspace"),
                                    workspace.numel(), _cfg(cfg), int(flags), _stream(stream)), "tm_merge_learned")
     return C, Cv, workspace

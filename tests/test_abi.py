@@ -157,3 +157,16 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
     # the allocation-free merge: lengths, key type, alignment
     assert lib.tm_merge_noalloc(0, k8, v4, -1, k8, v4, 1, k8, v4, None, None, None) == INV
     assert lib.tm_merge_noalloc(9, k8, v4, 1, k8, v4, 1, k8, v4, None, None, None) == UNS
+
+
+def test_binding_rejects_wrong_dtypes_before_the_device_check():
+    import torch
+    with pytest.raises(ValueError, match="dtype"):
+        tm._dev(torch.zeros(4, dtype=torch.int64), "Av", tm.PAYLOAD_DTYPES)      # payloads are 32-bit words
+    with pytest.raises(ValueError, match="dtype"):
+        tm._dev(torch.zeros(4, dtype=torch.float32), "A", tm.TORCH_KEY_DTYPES["i32"])
+    with pytest.raises(ValueError, match="contiguous"):
+        tm._dev(torch.zeros(4, 2, dtype=torch.int32).t(), "A", tm.TORCH_KEY_DTYPES["i32"])
+    with pytest.raises(ValueError, match="CUDA"):
+        tm._dev(torch.zeros(4, dtype=torch.int32), "Av", tm.PAYLOAD_DTYPES)
+    assert tm._dev(None, "Av", tm.PAYLOAD_DTYPES) == 0                           # keys-only call
