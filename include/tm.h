@@ -173,13 +173,14 @@ TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg
  * tm_plan_subproblems and tm_merge_tiles on the workspace's arrays.
  * Small merges (p <= 16384 and default in-CTA settings: no cfg->threads,
  * stages, grid, split other than the default, wait_ms or test_drop_tile)
- * run instead as one cooperative launch of the tile kernel: its threads do
- * the 2p + 1 searches, a grid-wide barrier (bounded wait: TM_ERR_TIMEOUT)
- * stands for the synchronisation, and each CTA then derives the
- * subproblems of the blocks it takes (Steps 3-4) and merges them; the
- * result is identical and the tile records of the workspace are not
- * written.  cfg->unfused = 1 keeps the separate launches.  The control
- * block (status word in its first 4 bytes) is cleared by this call. */
+ * run instead as one cooperative launch of the tile kernel: its warps do
+ * the 2p searches (one warp per search, 32 probes per round), a grid-wide
+ * barrier (bounded wait: TM_ERR_TIMEOUT) stands for the synchronisation,
+ * the grid writes the 2p tile records (Steps 3-4 selection) into the
+ * workspace, a second barrier follows, and the CTAs merge the records from
+ * the work queue; the result is identical.  cfg->unfused = 1 keeps the
+ * separate launches.  The control block (status word in its first 4 bytes)
+ * is cleared by this call. */
 TM_API tm_status tm_merge(tm_key_type kt,
                    const void* a_keys, const uint32_t* a_vals, int64_t n,
                    const void* b_keys, const uint32_t* b_vals, int64_t m,

@@ -170,3 +170,27 @@ def test_binding_rejects_wrong_dtypes_before_the_device_check():
     with pytest.raises(ValueError, match="CUDA"):
         tm._dev(torch.zeros(4, dtype=torch.int32), "Av", tm.PAYLOAD_DTYPES)
     assert tm._dev(None, "Av", tm.PAYLOAD_DTYPES) == 0                           # keys-only call
+
+
+def test_host_sizing_against_the_oracles_subproblems(lib):
+    """tm_plan_tile_count is the number of non-empty blocks of A and B (one
+    record each) and tm_merge_tile_cap bounds every subproblem the five
+    cases produce (Section 2: one A-block piece plus one B-block piece),
+    on random and tie-heavy inputs."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(21)
+    for trial in range(300):
+        n, m = int(rng.integers(0, 60)), int(rng.integers(0, 60))
+        p = int(rng.integers(1, 20))
+        alphabet = int(rng.choice([1, 2, 5, 1000]))
+        A = np.sort(rng.integers(0, alphabet, size=n)).astype(np.uint32)
+        B = np.sort(rng.integers(0, alphabet, size=m)).astype(np.uint32)
+        nonempty = sum(oracle.block_start(n, p, i) < n for i in range(p)) + \
+            sum(oracle.block_start(m, p, j) < m for j in range(p))
+        assert lib.tm_plan_tile_count(n, m, p) == nonempty
+        _, _, _, _, table = oracle.paper_merge(A, np.zeros(n, np.uint32), B, np.zeros(m, np.uint32), p)
+        sizes = (table[:, 1] - table[:, 0]) + (table[:, 3] - table[:, 2])
+        cap = lib.tm_merge_tile_cap(n, m, p)
+        assert cap == -(-n // p) + -(-m // p)
+        assert sizes.max(initial=0) <= cap and sizes.sum() == n + m
