@@ -138,8 +138,9 @@ TM_API const char* tm_status_str(tm_status s);
 TM_API int tm_version(void);
 
 /* Name of the CUDA error behind the calling thread's most recent
- * TM_ERR_CUDA from a launch of this library ("cudaSuccess" if none was
- * recorded; static storage). */
+ * TM_ERR_CUDA (a kernel launch or CUDA runtime call of this library that
+ * failed: memset, copy, event, graph or stream call); "cudaSuccess" if none
+ * was recorded.  Static storage. */
 TM_API const char* tm_last_cuda_error(void);
 
 /* ------------------------------------------------------------------------ */
