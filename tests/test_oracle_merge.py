@@ -384,3 +384,42 @@ def test_merge_sort_against_stable_sort(run, n):
     assert np.array_equal(K, keys[order]) and np.array_equal(V, vals[order])
     ref = sorted(zip(keys.tolist(), vals.tolist()), key=lambda t: t[0])
     assert K.tolist() == [k for k, _ in ref] and V.tolist() == [v for _, v in ref]
+
+
+# ---------------------------------------------------------------------------
+# The property check used at sizes no reference output fits (tests/helpers)
+# ---------------------------------------------------------------------------
+
+def test_property_check_accepts_the_oracle_and_rejects_planted_mistakes():
+    import torch
+    from tests.helpers import stable_merge_violation
+    rng = np.random.default_rng(31)
+    for alphabet, dtype, unsigned in ((1 << 30, np.int32, False), (50, np.int32, False), (1, np.int32, False),
+                                      (1 << 31, np.uint32, True), (1000, np.float32, False)):
+        n, m = 300001, 200003
+        A = rand_sorted(rng, n, dtype, alphabet)
+        B = rand_sorted(rng, m, dtype, alphabet)
+        Av, Bv = payloads(n, m)
+        C, Cv = oracle.merge_two_pointer(A, Av, B, Bv)
+        as_t = lambda x: torch.from_numpy(x.view(np.int32) if x.dtype == np.uint32 else x)
+        tA, tB, tC, tCv = as_t(A), as_t(B), as_t(C), as_t(Cv)
+        assert stable_merge_violation(tA, tB, tC, tCv, unsigned=unsigned, chunk=1 << 16) is None
+        # an A and a B element with the same key exchanged (B before A on a tie)
+        if alphabet <= 50:
+            k = next(k for k in range(n + m - 1) if C[k] == C[k + 1] and (Cv[k] >> 31) == 0 and (Cv[k + 1] >> 31) == 1)
+            bad = tCv.clone()
+            bad[k], bad[k + 1] = tCv[k + 1], tCv[k]
+            assert stable_merge_violation(tA, tB, tC, bad, unsigned=unsigned)[0] == k
+        # an element duplicated in place of its neighbour (one input lost)
+        bad_k, bad_v = tC.clone(), tCv.clone()
+        bad_k[70000], bad_v[70000] = tC[69999], tCv[69999]
+        assert stable_merge_violation(tA, tB, bad_k, bad_v, unsigned=unsigned, chunk=1 << 16)[0] == 69999
+        # a payload that does not travel with its key
+        bad_v = tCv.clone()
+        bad_v[123457] = tCv[123457] ^ 1 if (int(tCv[123457]) & 0x7FFFFFFF) ^ 1 < n else tCv[123457] - 1
+        assert stable_merge_violation(tA, tB, tC, bad_v, unsigned=unsigned) is not None
+        # a key one unit off at a chunk boundary
+        if dtype != np.float32:
+            bad_k = tC.clone()
+            bad_k[1 << 16] += 1
+            assert stable_merge_violation(tA, tB, bad_k, tCv, unsigned=unsigned, chunk=1 << 16)[0] == 1 << 16
