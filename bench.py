@@ -269,6 +269,55 @@ def cpu_baseline(items):
                                "outputs_equal_e2e": bool(same_par)}}
 
 
+def cpu_sort_baseline(log2n: int = 22):
+    """The oracle's stable merge sort (bottom-up from runs of one element,
+    oracle/tm_oracle.c), as it stands, on one host core, over a bounded
+    sample of the sort workload: 2**log2n u64 keys of the same distribution
+    (uniform in [0, 2**24)) with index payloads, sorted once; checked
+    against numpy's stable sort."""
+    import oracle
+    from paper_1202_6575_gb300 import workloads as W
+    n = 1 << log2n
+    keys, vals = W.sort_input("cpu", n=n)
+    hk, hv = keys.numpy().view(np.uint64), vals.numpy().view(np.uint32)
+    t0 = time.perf_counter()
+    k, v = oracle.merge_sort(hk, hv, run=1)
+    dt = time.perf_counter() - t0
+    order = np.argsort(hk, kind="stable")
+    return {"value": n / dt, "unit": "sorted elems/s", "cores": 1, "kind": "oracle",
+            "sample": f"2^{log2n} keys of the same distribution, sorted once (bottom-up merge sort)",
+            "seconds": dt, "equal_numpy_stable_sort": bool(np.array_equal(k, hk[order]) and
+                                                           np.array_equal(v, hv[order]))}
+
+
+def cpu_batched_baseline(pairs: int = 2048):
+    """The oracle's independent two-pointer merges, as they stand, on one
+    host core, over a bounded sample of the batched workload: `pairs` pairs
+    of the same length distribution (log-uniform in [1, 2**16] per side, u64
+    keys), merged once."""
+    import oracle
+    from paper_1202_6575_gb300 import workloads as W
+    a_off, A, Av, b_off, B, Bv = W.batched_pairs("cpu", pairs=pairs)
+    total = A.numel() + B.numel()
+    args = (a_off.numpy(), A.numpy().view(np.uint64), Av.numpy().view(np.uint32),
+            b_off.numpy(), B.numpy().view(np.uint64), Bv.numpy().view(np.uint32))
+    t0 = time.perf_counter()
+    oracle.merge_batched(*args)
+    dt = time.perf_counter() - t0
+    return {"value": total / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{pairs} pairs of the same length distribution ({total:,} elements), merged once",
+            "seconds": dt}
+
+
+def guarded(fn, *args, **kwargs):
+    """fn's result, or its error as a one-line record (a report extra must
+    not lose the benchmark line)."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:                              # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def bench_small_merge(dev, steps: int = 200):
     """The 1M merge: A n = 2**20, B m = 2**19 u32 keys in [0, 2**16), p = 1024
     blocks per input; one tm_merge captured in a CUDA graph and replayed (a
@@ -872,6 +921,9 @@ def main():
                  "partition_ablation": bench_partition(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            forms["batched"]["cpu_baseline"] = guarded(cpu_batched_baseline)
+            forms["merge_sort"]["cpu_baseline"] = guarded(cpu_sort_baseline)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,

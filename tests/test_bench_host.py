@@ -91,3 +91,12 @@ def test_reference_arm_json_line_on_a_small_sample():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baselines_of_the_sort_and_batched_forms():
+    s = bench.cpu_sort_baseline(log2n=16)
+    assert s["value"] > 0 and s["cores"] == 1 and s["kind"] == "oracle" and s["equal_numpy_stable_sort"]
+    b = bench.cpu_batched_baseline(pairs=64)
+    assert b["value"] > 0 and b["cores"] == 1 and b["kind"] == "oracle"
+    assert bench.guarded(lambda: 1 // 0) == {"error": "ZeroDivisionError: integer division or modulo by zero"}
+    assert bench.guarded(lambda x: x + 1, 1) == 2
