@@ -309,6 +309,29 @@ def cpu_batched_baseline(pairs: int = 2048):
             "seconds": dt}
 
 
+def cpu_learned_baseline(log2_base: int = 24, merges: int = 16, log2_batch: int = 20):
+    """The oracle's two-pointer merge, as it stands, on one host core, over a
+    bounded sample of the LSM workload: a 2**log2_base base of the same
+    mixture merged `merges` times with its sorted 2**log2_batch batches
+    (base' = merge(base, batch), the base on the A side).  The oracle needs
+    no model: its rate per merged element is that of any plain merge."""
+    import oracle
+    from paper_1202_6575_gb300 import workloads as W
+    N0, m = 1 << log2_base, 1 << log2_batch
+    X, Xv = W.lsm_base("cpu", n=N0)
+    base, base_v = X.numpy(), Xv.numpy().view(np.uint32)
+    elems, dt = 0, 0.0
+    for k in range(merges):
+        B, Bv = W.lsm_batch(k, "cpu", size=m, base_n=N0)
+        t0 = time.perf_counter()
+        base, base_v = oracle.merge_two_pointer(base, base_v, B.numpy(), Bv.numpy().view(np.uint32))
+        dt += time.perf_counter() - t0
+        elems += len(base)
+    return {"value": elems / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"base 2^{log2_base} of the same mixture merged {merges} times with sorted 2^{log2_batch} "
+                      "batches (two-pointer merge)", "seconds": dt}
+
+
 def guarded(fn, *args, **kwargs):
     """fn's result, or its error as a one-line record (a report extra must
     not lose the benchmark line)."""
@@ -924,6 +947,7 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             forms["batched"]["cpu_baseline"] = guarded(cpu_batched_baseline)
             forms["merge_sort"]["cpu_baseline"] = guarded(cpu_sort_baseline)
+            forms["learned"]["cpu_baseline"] = guarded(cpu_learned_baseline)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,

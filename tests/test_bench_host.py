@@ -100,3 +100,8 @@ def test_cpu_baselines_of_the_sort_and_batched_forms():
     assert b["value"] > 0 and b["cores"] == 1 and b["kind"] == "oracle"
     assert bench.guarded(lambda: 1 // 0) == {"error": "ZeroDivisionError: integer division or modulo by zero"}
     assert bench.guarded(lambda x: x + 1, 1) == 2
+
+
+def test_cpu_baseline_of_the_lsm_form():
+    d = bench.cpu_learned_baseline(log2_base=16, merges=3, log2_batch=10)
+    assert d["value"] > 0 and d["cores"] == 1 and d["kind"] == "oracle" and "2^16" in d["sample"]
