@@ -194,3 +194,21 @@ def test_host_sizing_against_the_oracles_subproblems(lib):
         cap = lib.tm_merge_tile_cap(n, m, p)
         assert cap == -(-n // p) + -(-m // p)
         assert sizes.max(initial=0) <= cap and sizes.sum() == n + m
+
+
+def test_header_is_c99_and_links_from_c(lib, tmp_path):
+    """include/tm.h compiles as strict C99 and a C program links against
+    libtm.so and calls its host-only entry points and argument checks."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_c_client")
+    libdir = os.path.dirname(tm.LIB_PATH)
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I" + os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "host", "abi_c_client.c"),
+                           tm.LIB_PATH, "-Wl,-rpath," + libdir, "-o", exe])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip().endswith("all ok"), r.stdout + r.stderr
