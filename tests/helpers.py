@@ -68,3 +68,39 @@ def stable_merge_violation(A, B, C, Cv, unsigned=False, chunk=1 << 24):
             return (s + int(bad[0]) - (1 if prev_key is not None else 0), "order of (key, tag)")
         prev_key, prev_tag = key[-1:], tag[-1:]
     return None
+
+
+def stable_sort_violation(src_keys, keys, vals, unsigned=False, chunk=1 << 24):
+    """First place where (keys, vals) fail to be the stable sort of
+    src_keys with payload = original index, or None.  Torch tensors of any
+    device, checked in chunks: every payload is an index of src_keys whose
+    key the output carries, and (key, index) strictly increases along the
+    output (keys non-decreasing, equal keys in input order).  n distinct
+    indices in that order are exactly the unique stable sort.  Returns
+    (position, reason)."""
+    import torch
+    n = src_keys.numel()
+    if keys.numel() != n or vals.numel() != n:
+        return (0, "length")
+    prev_key = prev_idx = None
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        key = keys[s:e]
+        idx = vals[s:e].to(torch.int64) & 0xFFFFFFFF
+        bad = torch.nonzero(idx >= n)
+        if bad.numel():
+            return (s + int(bad[0]), "payload is no input index")
+        bad = torch.nonzero(src_keys[idx] != key)
+        if bad.numel():
+            return (s + int(bad[0]), "key differs from the input element its payload names")
+        if unsigned:
+            key = key.to(torch.int64) & 0xFFFFFFFF
+        if prev_key is not None:
+            key = torch.cat([prev_key, key])
+            idx = torch.cat([prev_idx, idx])
+        lo_k, hi_k, lo_i, hi_i = key[:-1], key[1:], idx[:-1], idx[1:]
+        bad = torch.nonzero(~((lo_k < hi_k) | ((lo_k == hi_k) & (lo_i < hi_i))))
+        if bad.numel():
+            return (s + int(bad[0]) - (1 if prev_key is not None else 0), "order of (key, index)")
+        prev_key, prev_idx = key[-1:], idx[-1:]
+    return None

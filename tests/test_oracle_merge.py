@@ -423,3 +423,31 @@ def test_property_check_accepts_the_oracle_and_rejects_planted_mistakes():
             bad_k = tC.clone()
             bad_k[1 << 16] += 1
             assert stable_merge_violation(tA, tB, bad_k, tCv, unsigned=unsigned, chunk=1 << 16)[0] == 1 << 16
+
+
+def test_sort_property_check_accepts_the_oracle_and_rejects_planted_mistakes():
+    import torch
+    from tests.helpers import stable_sort_violation
+    rng = np.random.default_rng(33)
+    n = 400003
+    for keys, unsigned in ((rng.integers(0, 1 << 24, size=n).astype(np.uint64), False),
+                           (rng.integers(0, 7, size=n).astype(np.uint64), False),
+                           (rng.integers(0, 1 << 32, size=n).astype(np.uint32), True)):
+        vals = np.arange(n, dtype=np.uint32)
+        K, V = oracle.merge_sort(keys, vals, run=16)
+        assert np.array_equal(K, keys[np.argsort(keys, kind="stable")])
+        as_t = lambda x: torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else x.view(np.int32))
+        tS, tK, tV = as_t(keys), as_t(K), as_t(V)
+        assert stable_sort_violation(tS, tK, tV, unsigned=unsigned, chunk=1 << 16) is None
+        eq = np.nonzero(K[1:] == K[:-1])[0]
+        k = int(eq[len(eq) // 2])                       # two equal keys out of input order
+        bad = tV.clone()
+        bad[k], bad[k + 1] = tV[k + 1], tV[k]
+        assert stable_sort_violation(tS, tK, bad, unsigned=unsigned, chunk=1 << 16)[0] == k
+        bad = tV.clone()                                 # an index used twice, another lost
+        bad[(1 << 16) + 5] = tV[(1 << 16) + 4]
+        assert stable_sort_violation(tS, tK, bad, unsigned=unsigned, chunk=1 << 16) is not None
+        bad = tK.clone()                                 # keys out of order at a chunk boundary
+        bad[1 << 16], bad[(1 << 16) - 1] = tK[(1 << 16) - 1], tK[1 << 16]
+        if K[1 << 16] != K[(1 << 16) - 1]:
+            assert stable_sort_violation(tS, bad, tV, unsigned=unsigned, chunk=1 << 16) is not None
