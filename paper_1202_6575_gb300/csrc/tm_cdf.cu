@@ -26,6 +26,7 @@
 // merged output is therefore exactly the plain method's, whatever the model.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "tm_engine.cuh"
@@ -51,6 +52,14 @@ struct CdfHeader {
     float loss;
     uint32_t arrived;                  // CTAs of a learned search that finished reading the ranks (0 between calls)
 };
+// The byte layout include/tm.h documents for the model header (the binding
+// reads it at these offsets).
+static_assert(offsetof(CdfHeader, S) == 0 && offsetof(CdfHeader, H) == 4 && offsetof(CdfHeader, eps_frac) == 8 &&
+              offsetof(CdfHeader, cur) == 12 && offsetof(CdfHeader, N) == 16 &&
+              offsetof(CdfHeader, fallbacks) == 24 && offsetof(CdfHeader, learned) == 32 &&
+              offsetof(CdfHeader, adam_step) == 40 && offsetof(CdfHeader, loss) == 48 &&
+              offsetof(CdfHeader, arrived) == 52 && sizeof(CdfHeader) <= 256,
+              "model header layout differs from the one documented in tm.h");
 
 struct CdfLayout {
     size_t K, R0, R1, params, m, v, grad, eps_seg, bytes;

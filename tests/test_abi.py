@@ -212,3 +212,23 @@ def test_header_is_c99_and_links_from_c(lib, tmp_path):
                            tm.LIB_PATH, "-Wl,-rpath," + libdir, "-o", exe])
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip().endswith("all ok"), r.stdout + r.stderr
+
+
+def test_binding_struct_matches_the_c_layout(tmp_path):
+    """tm.TmConfig (ctypes) has the field names, offsets and sizes a C
+    compiler gives struct tm_config of include/tm.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_layout")
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "host", "abi_layout.c"), "-o", exe])
+    lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    c_fields = [ln.split() for ln in lines if ln and not ln.startswith("sizeof")]
+    c_size = int(next(ln for ln in lines if ln.startswith("sizeof")).split()[1])
+    py_fields = [(name, getattr(tm.TmConfig, name).offset, getattr(tm.TmConfig, name).size)
+                 for name, _ in tm.TmConfig._fields_]
+    assert [(n, int(o), int(s)) for n, o, s in c_fields] == py_fields
+    assert c_size == ctypes.sizeof(tm.TmConfig)
