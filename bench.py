@@ -45,7 +45,9 @@ import torch
 METRIC = "merged key+value elems/s and % of HBM peak, plain vs batched/learned, bit-exact"
 WORKLOAD = ("stable merge, int32 keys + int32 payloads: n=m=2^28 x {uniform_full, uniform_1024, "
             "all_equal, zipf_1.2}, plus skewed n=2^28, m=2^18 x the same four; pre-sorted")
+WORKLOAD_SHORT = "stable merge i32 keys+payloads: n=m=2^28 x 4 dists + skewed n=2^28, m=2^18 x 4"
 UNIT = "elems/s"
+NOMINAL_HBM_GBS = 8000.0
 
 
 def env_rank():
@@ -330,6 +332,85 @@ def cpu_learned_baseline(log2_base: int = 24, merges: int = 16, log2_batch: int 
     return {"value": elems / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"base 2^{log2_base} of the same mixture merged {merges} times with sorted 2^{log2_batch} "
                       "batches (two-pointer merge)", "seconds": dt}
+
+
+def _r(x, digits=4):
+    """x rounded to `digits` significant digits (None and non-numbers pass)."""
+    if isinstance(x, (bool, int)) or not isinstance(x, float):   # counts stay exact
+        return x
+    if x == 0 or not np.isfinite(x):
+        return float(x)
+    return float(f"{x:.{digits}g}")
+
+
+def compact_forms(forms: dict, peak_gbs: float) -> dict:
+    """The figures of every side form that the one-line result keeps: value,
+    time, fraction of the measured copy bandwidth, the CPU baseline's value
+    and the exactness flag.  Everything else (per-merge times, ablation
+    detail, configurations) goes to the detail line printed before it."""
+    if not forms:
+        return forms
+    out = {}
+    g = lambda d, k: (d or {}).get(k) if isinstance(d, dict) else None
+    f = forms.get("merge_1m_p1024")
+    if isinstance(f, dict) and "error" not in f:
+        out["merge_1m_p1024"] = {"value": _r(f.get("value")), "us": _r(f.get("us_per_merge")),
+                                 "frac_of_hbm": _r(g(f, "gbs") / peak_gbs if g(f, "gbs") else None),
+                                 "separate_us": _r(g(g(f, "separate_launches"), "us_per_merge")),
+                                 "phases_us": {k: _r(v, 3) for k, v in (g(f, "phases_us") or {}).items()} or None}
+    f = forms.get("batched")
+    if isinstance(f, dict) and "error" not in f:
+        out["batched"] = {"value": _r(f.get("value")), "ms": _r(f.get("ms")), "frac_of_hbm": _r(f.get("frac_of_hbm")),
+                          "cpu": _r(g(g(f, "cpu_baseline"), "value")), "bit_exact": f.get("bit_exact")}
+    f = forms.get("merge_sort")
+    if isinstance(f, dict) and "error" not in f:
+        out["merge_sort"] = {"value": _r(f.get("value")), "ms": _r(f.get("ms")),
+                             "frac_of_hbm": _r(f.get("frac_of_hbm")), "run_ms": _r(f.get("run_formation_ms")),
+                             "cpu": _r(g(g(f, "cpu_baseline"), "value")), "bit_exact": f.get("bit_exact")}
+    f = forms.get("keys_only")
+    if isinstance(f, dict) and "error" not in f:
+        out["keys_only"] = {d: {"value": _r(g(f[d], "value")), "ms": _r(g(f[d], "ms")),
+                                "frac_of_hbm": _r(g(f[d], "frac_of_hbm"))}
+                            for d in ("uniform_full", "uniform_1024") if d in f}
+    f = forms.get("learned")
+    if isinstance(f, dict) and "error" not in f:
+        out["learned"] = {"value": _r(g(g(f, "learned"), "value")), "plain_value": _r(g(g(f, "plain"), "value")),
+                          "e2e_speedup": _r(f.get("end_to_end_speedup")),
+                          "search_speedup": _r(f.get("search_speedup")),
+                          "search_speedup_pla_only": _r(f.get("search_speedup_pla_only")),
+                          "fallbacks": g(g(f, "learned"), "fallbacks"), "bit_identical": f.get("bit_identical"),
+                          "cpu": _r(g(g(f, "cpu_baseline"), "value"))}
+    f = forms.get("partition_ablation")
+    if isinstance(f, dict) and "error" not in f:
+        out["partition_ablation"] = {"equal_output_over_blocks": _r(f.get("equal_output_over_blocks"))}
+    for k, f in forms.items():                         # a form that failed keeps its one-line error
+        if isinstance(f, dict) and "error" in f:
+            out[k] = {"error": str(f["error"])[:160]}
+    return out
+
+
+def compact_line(line: dict, peak_gbs: float) -> dict:
+    """The result line with its long parts shortened: the side forms reduced
+    by compact_forms, the baselines' descriptions cut, numbers rounded."""
+    out = dict(line)
+    out["forms"] = compact_forms(line.get("forms"), peak_gbs)
+    cpu = line.get("cpu_baseline")
+    if isinstance(cpu, dict):
+        c = {k: _r(cpu.get(k)) for k in ("value", "unit", "cores", "kind")}
+        c["sample"] = "the eight merges once, two-pointer oracle"
+        c["e2e_outputs_equal_oracle"] = cpu.get("e2e_outputs_equal_oracle")
+        pp = cpu.get("paper_parallel")
+        if isinstance(pp, dict):
+            c["paper_parallel"] = {"value": _r(pp.get("value")), "cores": pp.get("cores")}
+        out["cpu_baseline"] = c
+    e2e = line.get("e2e")
+    if isinstance(e2e, dict):
+        out["e2e"] = {k: _r(v) for k, v in e2e.items() if k != "path"}
+    rl = line.get("roofline")
+    if isinstance(rl, dict):
+        out["roofline"] = {k: _r(v, 5) for k, v in rl.items() if k not in ("traffic_source", "peak_kind")}
+        out["roofline"]["peak_kind"] = "measured copy" if "measured" in str(rl.get("peak_kind")) else "fallback"
+    return out
 
 
 def guarded(fn, *args, **kwargs):
@@ -793,6 +874,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     elems_per_step = sum(it["n"] + it["m"] for it in items)
     bytes_merge_per_step = sum(2 * (it["n"] + it["m"]) * 8 for it in items)
+    # algorithmic search bytes: ceil(log2(len + 1)) probes of 4 B per search,
+    # p searches into each array
+    search_bytes_per_step = sum(it["p"] * 4 * (int(it["n"]).bit_length() + int(it["m"]).bit_length())
+                                for it in items)
 
     # per-merge events: search start, plan start, merge start, merge end
     def step(evs=None):
@@ -852,7 +937,12 @@ def main():
                 "traffic": traffic, "traffic_source": traffic_src,
                 "algorithmic_bytes_per_launch": bytes_merge_per_step / len(items),
                 "search_share": search_ms / (search_ms + plan_ms + merge_ms),
-                "plan_share": plan_ms / (search_ms + plan_ms + merge_ms)}
+                "plan_share": plan_ms / (search_ms + plan_ms + merge_ms),
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                # whole step: merge bytes plus the searches' probe bytes (one
+                # 4-byte key per probe) over search + plan + merge time
+                "step_frac": (bytes_merge_per_step + search_bytes_per_step) * args.steps /
+                             ((search_ms + plan_ms + merge_ms) / 1e3) / 1e9 / peak}
 
     # End to end: pinned host inputs -> device, merge through tm_merge, result
     # -> host, for every merge of the step.  Copies in, merges and copies out
@@ -953,17 +1043,20 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "elements_per_step": elems_per_step,
+                "config": {"workload": WORKLOAD_SHORT, "elements_per_step": elems_per_step,
                            "merges_per_step": n_merges, "tile": args.tile or 2048,
                            "blocks_p": p_first,
                            "threads": args.threads or 128, "stages": args.stages or "auto",
-                           "split": {0: "diagonal (default)", 1: "blocks", 2: "diagonal"}[args.split], "l2": "inputs larger than L2 (2-4 GB per merge)",
-                           "parallelism": f"replicas x{world}"},
-                "per_merge_ms": per_item_merge_ms,
+                           "split": {0: "diagonal (default)", 1: "blocks", 2: "diagonal"}[args.split],
+                           "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
                 "forms": forms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * n_merges * args.steps}
-        print(json.dumps(line), flush=True)
+        # Every figure first, on a line of its own that is not JSON; then the
+        # result line, short enough to survive a truncated log.
+        detail = dict(line, per_merge_ms=per_item_merge_ms, config=dict(line["config"], workload=WORKLOAD))
+        print("detail " + json.dumps(detail), flush=True)
+        print(json.dumps(compact_line(line, peak), separators=(",", ":")), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

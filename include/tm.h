@@ -425,12 +425,17 @@ TM_API tm_status tm_merge_learned(void* model, int segments, int hidden,
  * tm_merge_blocks() <= 262143 (about 2^29 elements at the default tile);
  * larger requests return TM_ERR_WORKSPACE and launch nothing.
  * The first call on each device looks the array's device address up once
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress), and again after the device's context changes
+ * (cudaDeviceReset); make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents: two
  * calls that overlap on the GPU (other streams, other host threads) race and
  * corrupt each other's result, so keep calls ordered on one stream.
  * `status` (device int32, may be NULL) is an output: the call clears it and
- * a kernel sets it on a device-side error, as the status word of tm_merge. */
+ * a kernel sets it on a device-side error, as the status word of tm_merge.
+ * Of tm_config it reads p, tile and threads (128, 256 or 512); it always
+ * merges with one CTA per subproblem, so split, stages, grid and unfused do
+ * not apply, and partition must be TM_PARTITION_BLOCKS (anything else, and a
+ * thread count tm_merge refuses, returns TM_ERR_UNSUPPORTED). */
 TM_API tm_status tm_merge_noalloc(tm_key_type kt,
                                   const void* a_keys, const uint32_t* a_vals, int64_t n,
                                   const void* b_keys, const uint32_t* b_vals, int64_t m,

@@ -469,7 +469,7 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
         if (in_v) sv[i] = in_v[base + i];
     }
     __syncthreads();
-    // blocked registers: thread t holds elements [8t, 8t + 8); missing ones
+    // blocked registers: thread t holds elements [kSortVT*t, kSortVT*(t+1)); missing ones
     // (past len) are marked invalid and sort to the end
     K k[kSortVT];
     uint32_t v[kSortVT];
@@ -482,7 +482,7 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
         v[q] = 0u;
         if (ok[q]) { k[q] = sk[i]; v[q] = sv[i]; }
     }
-    // stable odd-even transposition sort of 8 (invalid elements are largest)
+    // stable odd-even transposition sort of kSortVT (invalid elements are largest)
 #pragma unroll
     for (int r = 0; r < kSortVT; ++r) {
 #pragma unroll

@@ -601,21 +601,46 @@ constexpr int64_t kNoAllocMaxBlocks = 262143;            // p + 1 <= 262144 per 
 
 static __device__ __align__(256) int64_t g_noalloc_ranks[2 * (kNoAllocMaxBlocks + 1)];
 
-// Device address of g_noalloc_ranks on the current device, looked up once per
-// device (the host-side name of a __device__ array is not a device address).
+// The calling thread's current CUDA context, through the driver's
+// cuCtxGetCurrent (found once via the runtime, so the library does not link
+// libcuda); nullptr if it cannot be found.
+static void* current_context() {
+    using CtxGetCurrent = int (*)(void**);            // CUresult cuCtxGetCurrent(CUcontext*)
+    static CtxGetCurrent fn = []() -> CtxGetCurrent {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of g_noalloc_ranks for the current device and context,
+// looked up once per (device, context) with that device current: the
+// host-side name of a __device__ array is not a device address, and a
+// context created after cudaDeviceReset holds the array at a new address.
 static int64_t* noalloc_ranks_ptr() {
     static std::mutex mu;
+    static void* ctx_of[64] = {nullptr};
     static int64_t* addr[64] = {nullptr};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    void* ctx = current_context();                    // nullptr before the runtime's first use
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || ctx == nullptr || ctx != ctx_of[dev]) {
         void* p = nullptr;
         if (const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ranks); e != cudaSuccess) {
             record_cuda_error(e);
             return nullptr;
         }
         addr[dev] = static_cast<int64_t*>(p);
+        ctx_of[dev] = current_context();              // the lookup made the device's context current
     }
     return addr[dev];
 }
@@ -658,6 +683,10 @@ extern "C" tm_status tm_merge_noalloc(tm_key_type kt,
         (n + m > 0 && (!aligned(c_keys, E) || !aligned(c_vals, 4))) ||
         (status && !aligned(status, 4)))
         return c_vals == nullptr && a_vals == nullptr && b_vals == nullptr ? TM_ERR_UNSUPPORTED : TM_ERR_INVALID;
+    // one method only: the paper's blocks, one CTA per subproblem, 128, 256
+    // or 512 threads (split, stages, grid and unfused do not apply)
+    if (cfg && (cfg->partition != TM_PARTITION_BLOCKS || (cfg->threads && log2_threads(cfg) < 0)))
+        return TM_ERR_UNSUPPORTED;
     const int64_t p = choose_blocks(n, m, cfg);
     if (p > kNoAllocMaxBlocks) return TM_ERR_WORKSPACE;   // beyond the built-in array
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

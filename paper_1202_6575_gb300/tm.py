@@ -28,6 +28,8 @@ TM_ERR_WORKSPACE = 3
 TM_ERR_CUDA = 4
 TM_ERR_TIMEOUT = 5
 TM_ERR_BOUNDS = 6
+TM_PARTITION_BLOCKS = 0
+TM_PARTITION_DIAGONALS = 1
 
 SPLIT_BLOCKS = 1
 SPLIT_DIAGONAL = 2

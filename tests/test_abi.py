@@ -157,6 +157,10 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
     # the allocation-free merge: lengths, key type, alignment
     assert lib.tm_merge_noalloc(0, k8, v4, -1, k8, v4, 1, k8, v4, None, None, None) == INV
     assert lib.tm_merge_noalloc(9, k8, v4, 1, k8, v4, 1, k8, v4, None, None, None) == UNS
+    # configurations tm_merge refuses are refused here too (before any device work)
+    for bad in ({"partition": tm.TM_PARTITION_DIAGONALS}, {"partition": 7}, {"threads": 64}, {"threads": 384}):
+        c = tm.TmConfig(**bad)
+        assert lib.tm_merge_noalloc(0, k8, v4, 10, k8, v4, 10, k8, v4, None, ctypes.byref(c), None) == UNS, bad
 
 
 def test_binding_rejects_wrong_dtypes_before_the_device_check():

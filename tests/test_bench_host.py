@@ -105,3 +105,67 @@ def test_cpu_baselines_of_the_sort_and_batched_forms():
 def test_cpu_baseline_of_the_lsm_form():
     d = bench.cpu_learned_baseline(log2_base=16, merges=3, log2_batch=10)
     assert d["value"] > 0 and d["cores"] == 1 and d["kind"] == "oracle" and "2^16" in d["sample"]
+
+
+def _full_forms():
+    per = {f"m{k}": 1.2345678 for k in range(8)}
+    cpu = {"value": 7.1e8, "unit": "elems/s", "cores": 1, "kind": "oracle", "sample": "x" * 300, "seconds": 4.6}
+    return {
+        "merge_1m_p1024": {"workload": "w" * 200, "elements": 1572864, "us_per_merge": 27.1, "value": 5.8e10,
+                           "gbs": 928.0, "fused": {"us_per_merge": 27.1}, "separate_launches": {"us_per_merge": 36.0},
+                           "phases_us": {"search": 4.9, "barrier1": 1.5, "select": 2.5, "barrier2": 1.7,
+                                         "merge": 11.0}},
+        "batched": {"workload": "w" * 300, "value": 2.6e11, "ms": 2.97, "frac_of_hbm": 0.929, "config": {"tile": 2048},
+                    "cpu_baseline": cpu, "bit_exact": True, "speedup_vs_plain": 468.7},
+        "merge_sort": {"value": 1.17e10, "ms": 23.0, "frac_of_hbm": 0.79, "run_formation_ms": 4.26,
+                       "cpu_baseline": cpu, "bit_exact": True},
+        "keys_only": {"uniform_full": {"ms": 1.24, "value": 4.3e11, "gbs": 3460.0, "frac_of_hbm": 0.51},
+                      "uniform_1024": {"ms": 0.92, "value": 5.8e11, "gbs": 4660.0, "frac_of_hbm": 0.69}},
+        "partition_ablation": {"blocks": {"total_ms": 8.12, "per_merge_ms": per},
+                               "equal_output": {"total_ms": 8.63, "per_merge_ms": per},
+                               "equal_output_over_blocks": 1.063},
+        "learned": {"plain": {"value": 3.99e11, "search_ms_mean": 0.055}, "learned": {"value": 4.0e11, "fallbacks": 0},
+                    "search_speedup": 1.08, "search_speedup_pla_only": 1.07, "end_to_end_speedup": 1.004,
+                    "bit_identical": True, "cpu_baseline": cpu},
+    }
+
+
+def test_compact_line_keeps_every_form_and_stays_short():
+    line = {"metric": bench.METRIC, "value": 3.99e11, "unit": "elems/s", "n_gpus": 1, "steps": 200, "warmup": 5,
+            "ms_per_step": 8.07, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": bench.WORKLOAD_SHORT, "elements_per_step": 3222274048, "merges_per_step": 8,
+                       "tile": 2048, "blocks_p": 262144, "threads": 128, "stages": "auto",
+                       "split": "diagonal (default)", "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+            "forms": _full_forms(),
+            "roofline": {"bound": "hbm", "kernel": "merge_engine_kernel", "achieved": 6760.0065, "peak": 6703.8,
+                         "unit": "GB/s", "frac": 1.0083, "peak_kind": "measured hbm_gbs (copy)",
+                         "traffic": 6162599116.8, "traffic_source": "profiles/merge_engine_kernel_large_merge.md",
+                         "algorithmic_bytes_per_launch": 6444548096.0, "search_share": 0.0385,
+                         "plan_share": 0.0145, "frac_of_nominal": 0.845, "step_frac": 0.95},
+            "cpu_baseline": {"value": 7.0e8, "unit": "elems/s", "cores": 1, "kind": "oracle", "sample": "y" * 200,
+                             "seconds": 4.6, "e2e_outputs_equal_oracle": True,
+                             "paper_parallel": {"value": 9.6e9, "cores": 16, "sample": "z" * 100}},
+            "e2e": {"value": 1.6e10, "unit": "elems/s", "h2d_bytes_per_step": 25778192384,
+                    "d2h_bytes_per_step": 25778192384, "steps": 3, "path": "p" * 200},
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 12},
+            "gpu_launches": 4800}
+    c = bench.compact_line(line, 6703.8)
+    s = json.dumps(c, separators=(",", ":"))
+    assert len(s) < 2400, len(s)           # the driver keeps about the last 3000 characters
+    for form in ("merge_1m_p1024", "batched", "merge_sort", "keys_only", "learned", "partition_ablation"):
+        assert form in c["forms"]
+    assert c["forms"]["merge_1m_p1024"]["us"] == 27.1
+    assert c["forms"]["merge_1m_p1024"]["phases_us"]["merge"] == 11.0
+    assert c["forms"]["batched"]["frac_of_hbm"] == 0.929 and c["forms"]["batched"]["cpu"] == 7.1e8
+    assert c["forms"]["keys_only"]["uniform_full"]["frac_of_hbm"] == 0.51
+    assert c["forms"]["learned"]["search_speedup_pla_only"] == 1.07
+    for key in ("value", "ms_per_step", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches", "config"):
+        assert key in c
+    assert c["e2e"]["h2d_bytes_per_step"] == 25778192384
+    assert c["roofline"]["frac"] == 1.0083 and c["roofline"]["bound"] == "hbm"
+    # a failed form keeps a short error record
+    forms = _full_forms()
+    forms["batched"] = {"error": "RuntimeError: " + "e" * 500}
+    c2 = bench.compact_forms(forms, 6703.8)
+    assert c2["batched"]["error"].startswith("RuntimeError") and len(c2["batched"]["error"]) <= 160

@@ -4,13 +4,17 @@ Some callers cannot allocate device memory or hand the library a workspace
 (code hosted by a framework that passes it only input and output buffers,
 loops that must never hit the allocator).  tm_merge_noalloc keeps its cross
 ranks in a device array built into the library instead.  These tests call it
-through the C ABI and check it against tm_merge, bit for bit, on two calls in
-a row (the second call reuses the array the first one left behind).  The file
-is named so that pytest collects it last.
+through the C ABI and check it against tm_merge and against the CPU oracle's
+two-pointer stable merge, bit for bit, on two calls in a row (the second call
+reuses the array the first one left behind).  The file is named so that
+pytest collects it last.
 """
+import numpy as np
 import pytest
 import torch
 
+import oracle
+from tests.helpers import NP_KEY, vals_np
 from paper_1202_6575_gb300 import tm, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -43,6 +47,10 @@ def test_noalloc_matches_tm_merge_on_two_calls_in_a_row(kt, cfg):
         assert int(status.item()) == 0
         assert torch.equal(C, C_ref)
         assert torch.equal(Cv, Cv_ref)
+        K, V = oracle.merge_two_pointer(A.cpu().numpy().view(NP_KEY[kt]), vals_np(Av),
+                                        B.cpu().numpy().view(NP_KEY[kt]), vals_np(Bv))
+        assert np.array_equal(C.cpu().numpy().view(NP_KEY[kt]), K)
+        assert np.array_equal(vals_np(Cv), V)
 
 
 def test_noalloc_rejects_more_blocks_than_its_array_holds():
