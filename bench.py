@@ -468,6 +468,20 @@ def bench_small_merge(dev, steps: int = 200):
                               "memset, search, plan, memset, merge"}
     out.update({"us_per_merge": out["fused"]["us_per_merge"], "value": out["fused"]["value"],
                 "gbs": out["fused"]["gbs"]})
+    # where the fused launch spends its time: per-CTA %globaltimer stamps
+    # (tm_config.trace), L2 flushed before each of 20 traced calls, median
+    cfg = {"p": 1024, "trace": 1}
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
+    phases = []
+    for i in range(23):
+        flush.fill_(i & 255)
+        tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
+        ph = tm.tm_merge_phase_times(ws, n, m, cfg, stream=s)
+        if i >= 3:
+            phases.append(ph)
+    assert tm.tm_read_status(ws, stream=s) == 0
+    assert torch.equal(ref[0], C) and torch.equal(ref[1], Cv)
+    out["phases_us"] = {k: float(np.median([ph[k] for ph in phases])) for k in tm.PHASES}
     return out
 
 

@@ -108,6 +108,13 @@ typedef struct tm_config {
                            launches where the fused single launch would be used (below) */
     int32_t partition;  /* tm_merge only: TM_PARTITION_BLOCKS (0, the paper's method) or
                            TM_PARTITION_DIAGONALS (1, an ablation: equal output ranges) */
+    int32_t payload_bytes; /* bytes of one payload word: 4 (also 0, the default) or 8; with 8
+                           every payload pointer of the call points to 8-byte words (8-byte
+                           aligned) although it is declared uint32_t* */
+    int32_t trace;      /* tm_merge only, profiling (0 = off): 1 makes the fused single launch
+                           record per-CTA phase timestamps in the workspace (which then needs
+                           tm_merge_workspace_size with the same cfg); tm_merge_phase_times
+                           reads them */
     int32_t reserved;
 } tm_config;
 
@@ -188,6 +195,18 @@ TM_API tm_status tm_merge(tm_key_type kt,
                    void* c_keys, uint32_t* c_vals,
                    void* workspace, size_t workspace_bytes,
                    const tm_config* cfg, tm_stream_t stream);
+
+/* Phase times of the last fused single launch of tm_merge made with
+ * cfg->trace = 1 on this workspace (same n, m, cfg): synchronises `stream`,
+ * reads the per-CTA %globaltimer stamps and writes to us_out (host, 6
+ * doubles, microseconds): [0] Steps 1-2 searches (kernel entry of the first
+ * CTA to the last CTA done searching), [1] the synchronisation after them
+ * (grid barrier), [2] Steps 3-4 selection, [3] a second barrier (0 when the
+ * launch has none), [4] the merges (to the last CTA's last store), [5] the
+ * whole kernel.  TM_ERR_INVALID when the workspace holds no trace (the call
+ * did not take the fused launch, or cfg->trace was 0). */
+TM_API tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
+                                      double* us_out, tm_stream_t stream);
 
 /* Steps 1 and 2 alone (Section 2): xbar[i] = rank_low(A[x_i], B) for i < p,
  * xbar[p] = m; ybar[j] = rank_high(B[y_j], A) for j < p, ybar[p] = n, with

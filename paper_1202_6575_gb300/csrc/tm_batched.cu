@@ -683,6 +683,7 @@ tm_status tm_merge_batched(tm_key_type kt, int64_t num_pairs,
     tm_status st = check_batched(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
                                  total_b, c_keys, c_vals);
     if (st != TM_OK) return st;
+    if (payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     tm_config tuned;
     if (!cfg && tuned_config(1, kt, total_a + total_b, &tuned)) cfg = &tuned;
     if (!workspace || !aligned(workspace, 256) ||
@@ -700,7 +701,7 @@ size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg) {
 tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
                         void* workspace, size_t workspace_bytes, const tm_config* cfg, tm_stream_t stream) {
     if (n < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (n > 0 && (!aligned(keys, E) || !aligned(tmp_keys, E) ||
                   ((vals || tmp_vals) && (!aligned(vals, 4) || !aligned(tmp_vals, 4)))))

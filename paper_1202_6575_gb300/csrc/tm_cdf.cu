@@ -639,11 +639,12 @@ tm_status tm_merge_learned(void* model, int segments, int hidden,
                            const tm_config* cfg, int flags, tm_stream_t stream) {
     // every argument rule of the calls below, checked before anything is issued
     if (!model_ok(model, segments, hidden) || n < 1 || m < 0) return TM_ERR_INVALID;
+    if (payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     if (!aligned(a_keys, 4) || (m > 0 && !aligned(b_keys, 4)) || !aligned(c_keys, 4) ||
         !payloads_ok(n, a_vals, m, b_vals, c_vals))
         return TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
-    if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p))
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p, cfg))
         return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the workspace layout of tm_merge: control | xbar | ybar | tiles

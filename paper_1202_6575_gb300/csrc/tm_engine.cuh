@@ -204,7 +204,21 @@ struct EngineArgs {
     int64_t* fy;
     int64_t fp;
     unsigned int* gbar;
+    // Profiling (nullptr = off): trace[0] = gridDim.x, then kTraceSlots
+    // %globaltimer stamps per CTA from trace[kTraceSlots]: kernel entry,
+    // searches done, first barrier passed, selection done, second barrier
+    // passed, merges done.
+    uint64_t* trace;
 };
+
+constexpr int kTraceSlots = 8;
+
+__device__ __forceinline__ void trace_stamp(const EngineArgs& g, int slot) {
+    if (g.trace != nullptr && threadIdx.x == 0) {
+        g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + slot] = global_timer_ns();
+        if (slot == 0 && blockIdx.x == 0) g.trace[0] = gridDim.x;
+    }
+}
 
 // Bulk-copy window of elements [lo, lo+cnt) of an array (base, len,
 // element size E) into a region at byte offset `dst_off`: the region
@@ -692,12 +706,17 @@ merge_engine_kernel(const EngineArgs g) {
         fence_mbar_init();
         fence_proxy_async_smem();
     }
+    trace_stamp(g, 0);
     __syncthreads();
     if constexpr (FUSED) {                            // Steps 1-2, the single synchronisation, the plan
         fused_cross_ranks<K>(g);
+        trace_stamp(g, 1);
         if (!grid_barrier(g.gbar, 1, g.wait_ns, g.status)) return;
+        trace_stamp(g, 2);
         fused_plan(g);
+        trace_stamp(g, 3);
         if (!grid_barrier(g.gbar, 2, g.wait_ns, g.status)) return;
+        trace_stamp(g, 4);
     }
     if (tid >= T) {
         engine_producer<K, LOG_T, S_IN, SPLIT, FUSED>(g, smem, full, empty, tid - T);
@@ -708,6 +727,7 @@ merge_engine_kernel(const EngineArgs g) {
         else                 engine_consumers_diagonal<K, LOG_T, S_IN, VT, false>(g, smem, full, empty, tid);
     }
     else engine_consumers_blocks<K, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
+    trace_stamp(g, 5);
 }
 
 }  // namespace pmerge

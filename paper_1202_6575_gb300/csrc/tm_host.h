@@ -43,6 +43,13 @@ inline bool payloads_ok(int64_t n, const void* a, int64_t m, const void* b, cons
     return (n == 0 || aligned(a, 4)) && (m == 0 || aligned(b, 4)) && aligned(c, 4);
 }
 
+// Bytes of one payload word selected by cfg (tm_config.payload_bytes: 0 or 4
+// -> 4, 8 -> 8), -1 for anything else.
+inline int payload_size(const tm_config* cfg) {
+    const int b = cfg ? cfg->payload_bytes : 0;
+    return b == 0 ? 4 : ((b == 4 || b == 8) ? b : -1);
+}
+
 // Opt-in dynamic shared memory per CTA of the current device, capped at
 // kMaxSmemBytes.
 inline uint32_t device_smem_limit() {
@@ -99,7 +106,7 @@ inline int sm_count() {
 
 int64_t choose_blocks(int64_t n, int64_t m, const tm_config* cfg);
 int choose_threads(const tm_config* cfg);
-size_t merge_workspace_bytes(int64_t p);
+size_t merge_workspace_bytes(int64_t p, const tm_config* cfg);
 int log2_threads(const tm_config* cfg);
 tm_status merge_tiles_dispatch(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
                                const void* b_keys, const uint32_t* b_vals, int64_t m,

@@ -3,6 +3,7 @@
 // points.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "tm_engine.cuh"
 #include "tm_host.h"
@@ -345,10 +346,17 @@ static int64_t single_merge_tiles(int64_t n, int64_t m, int64_t p) {
     return (n < p ? n : p) + (m < p ? m : p);
 }
 
-// Workspace of tm_merge: [status int32 | queue u64 | grid-barrier count u32 | pad to 256] xbar ybar tiles.
-struct MergeWs { int32_t* status; void* control; int64_t* xbar; int64_t* ybar; TileDesc* tiles; size_t bytes; };
+// Workspace of tm_merge: [status int32 | queue u64 | grid-barrier count u32 | pad to 256] xbar ybar tiles
+// [trace: kTraceSlots u64 per CTA, plus a header row, when cfg->trace].
+struct MergeWs {
+    int32_t* status; void* control; int64_t* xbar; int64_t* ybar; TileDesc* tiles; uint64_t* trace; size_t bytes;
+};
 
-static MergeWs merge_ws_layout(void* base, int64_t p) {
+constexpr int64_t kTraceMaxCtas = 4096;
+
+static bool wants_trace(const tm_config* cfg) { return cfg && cfg->trace; }
+
+static MergeWs merge_ws_layout(void* base, int64_t p, bool trace) {
     MergeWs w;
     uint8_t* b = static_cast<uint8_t*>(base);
     size_t o = kStatusBytes;
@@ -357,11 +365,16 @@ static MergeWs merge_ws_layout(void* base, int64_t p) {
     w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(p + 1) * 8, 256);
     w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(p + 1) * 8, 256);
     w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)(2 * p) * sizeof(TileDesc), 256);
+    w.trace = nullptr;
+    if (trace) {
+        w.trace = reinterpret_cast<uint64_t*>(b + o);
+        o += align_up((size_t)(kTraceMaxCtas + 1) * kTraceSlots * 8, 256);
+    }
     w.bytes = o;
     return w;
 }
 
-size_t merge_workspace_bytes(int64_t p) { return merge_ws_layout(nullptr, p).bytes; }
+size_t merge_workspace_bytes(int64_t p, const tm_config* cfg) { return merge_ws_layout(nullptr, p, wants_trace(cfg)).bytes; }
 
 // The fused single launch applies to small merges with the default in-CTA
 // settings (it has one configuration: 128 consumer threads, diagonal split,
@@ -371,6 +384,7 @@ constexpr int64_t kFusedMaxCap = 17 * 128;
 
 static bool fused_applies(int64_t p, int64_t cap, const tm_config* cfg) {
     if (p > kFusedMaxBlocks || cap > kFusedMaxCap) return false;
+    if (sm_count() * 8 > kTraceMaxCtas) return false;  // more CTAs than a trace holds
     if (cfg && (cfg->unfused || cfg->partition || (cfg->threads && cfg->threads != 128) || cfg->stages || cfg->grid ||
                 (cfg->split && cfg->split != TM_SPLIT_DIAGONAL) || cfg->wait_ms || cfg->test_drop_tile))
         return false;
@@ -384,9 +398,12 @@ static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t*
                              const void* b_keys, const uint32_t* b_vals, int64_t m,
                              void* c_keys, uint32_t* c_vals, void* ws, int64_t p,
                              const tm_config* cfg, cudaStream_t s) {
-    MergeWs w = merge_ws_layout(ws, p);
+    MergeWs w = merge_ws_layout(ws, p, wants_trace(cfg));
     // status word, work-queue counter, grid-barrier count
     if (cudaError_t e = cudaMemsetAsync(w.control, 0, 32, s); e != cudaSuccess) return cuda_failed(e);
+    if (w.trace) {                                     // no trace until a fused launch writes one
+        if (cudaError_t e = cudaMemsetAsync(w.trace, 0, 8, s); e != cudaSuccess) return cuda_failed(e);
+    }
     if (n + m == 0) return TM_OK;
     if (log2_threads(cfg) < 0) return TM_ERR_UNSUPPORTED;
     const int64_t cap = single_merge_cap(n, m, p);
@@ -419,6 +436,7 @@ static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t*
         a.cap = (int)cap;
         a.fx = w.xbar; a.fy = w.ybar; a.fp = p;
         a.gbar = reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(w.control) + 16);
+        a.trace = w.trace;
         const tm_status st = launch_engine_fused<K>(a, s);
         if (st != TM_ERR_UNSUPPORTED) return st;       // else: the separate launches below
     }
@@ -470,7 +488,35 @@ int64_t tm_merge_blocks(int64_t n, int64_t m, const tm_config* cfg) {
 
 size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg) {
     if (n < 0 || m < 0) return 0;
-    return merge_workspace_bytes(choose_blocks(n, m, cfg));
+    return merge_workspace_bytes(choose_blocks(n, m, cfg), cfg);
+}
+
+tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
+                               double* us_out, tm_stream_t stream) {
+    if (n < 0 || m < 0 || !us_out || !wants_trace(cfg) || !aligned(workspace, 256)) return TM_ERR_INVALID;
+    const MergeWs w = merge_ws_layout(const_cast<void*>(workspace), choose_blocks(n, m, cfg), true);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (const cudaError_t e = cudaStreamSynchronize(s); e != cudaSuccess) return cuda_failed(e);
+    uint64_t grid = 0;
+    if (const cudaError_t e = cudaMemcpy(&grid, w.trace, 8, cudaMemcpyDeviceToHost); e != cudaSuccess)
+        return cuda_failed(e);
+    if (grid == 0 || grid > (uint64_t)kTraceMaxCtas) return TM_ERR_INVALID;
+    std::vector<uint64_t> t((size_t)grid * kTraceSlots);
+    if (const cudaError_t e = cudaMemcpy(t.data(), w.trace + kTraceSlots, t.size() * 8, cudaMemcpyDeviceToHost);
+        e != cudaSuccess)
+        return cuda_failed(e);
+    // phase ends: the last CTA to reach each stamp; start: the first entry
+    uint64_t start = UINT64_MAX, end[6] = {0, 0, 0, 0, 0, 0};
+    for (uint64_t c = 0; c < grid; ++c) {
+        const uint64_t* r = &t[(size_t)c * kTraceSlots];
+        start = std::min(start, r[0]);
+        for (int k = 1; k <= 5; ++k) end[k] = std::max(end[k], r[k]);
+    }
+    end[0] = start;
+    for (int k = 1; k <= 5; ++k) end[k] = std::max(end[k], end[k - 1]);   // a phase never ends before the last
+    for (int k = 0; k < 5; ++k) us_out[k] = (double)(end[k + 1] - end[k]) * 1e-3;
+    us_out[5] = (double)(end[5] - start) * 1e-3;
+    return TM_OK;
 }
 
 tm_status tm_merge(tm_key_type kt,
@@ -480,13 +526,13 @@ tm_status tm_merge(tm_key_type kt,
                    void* workspace, size_t workspace_bytes,
                    const tm_config* cfg, tm_stream_t stream) {
     if (n < 0 || m < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
         !payloads_ok(n, a_vals, m, b_vals, c_vals))
         return TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
-    if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p))
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p, cfg))
         return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (kt) {
@@ -546,7 +592,7 @@ tm_status tm_merge_tiles(tm_key_type kt,
                          void* c_keys, uint32_t* c_vals, void* control,
                          const tm_config* cfg, tm_stream_t stream) {
     if (n < 0 || m < 0 || n_tiles < 0 || cap < 1 || !aligned(control, 256)) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
         !payloads_ok(n, a_vals, m, b_vals, c_vals) || (n_tiles > 0 && !aligned(tiles, 16)))
@@ -685,7 +731,8 @@ extern "C" tm_status tm_merge_noalloc(tm_key_type kt,
         return c_vals == nullptr && a_vals == nullptr && b_vals == nullptr ? TM_ERR_UNSUPPORTED : TM_ERR_INVALID;
     // one method only: the paper's blocks, one CTA per subproblem, 128, 256
     // or 512 threads (split, stages, grid and unfused do not apply)
-    if (cfg && (cfg->partition != TM_PARTITION_BLOCKS || (cfg->threads && log2_threads(cfg) < 0)))
+    if (cfg && (cfg->partition != TM_PARTITION_BLOCKS || (cfg->threads && log2_threads(cfg) < 0) ||
+                payload_size(cfg) != 4))
         return TM_ERR_UNSUPPORTED;
     const int64_t p = choose_blocks(n, m, cfg);
     if (p > kNoAllocMaxBlocks) return TM_ERR_WORKSPACE;   // beyond the built-in array

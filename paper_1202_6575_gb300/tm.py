@@ -43,7 +43,8 @@ class TmConfig(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
                 ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("unfused", ctypes.c_int32),
-                ("partition", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("partition", ctypes.c_int32), ("payload_bytes", ctypes.c_int32), ("trace", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
@@ -74,6 +75,7 @@ _SIGNATURES = {
     "tm_rank_search": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I64, _P, _P]),
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "tm_merge_phase_times": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
     "tm_merge_batched_workspace_size": (_SZ, [_I64, _I64, _I64, _P]),
     "tm_merge_batched": (ctypes.c_int, [ctypes.c_int, _I64, _P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P, _SZ,
                                         _P, _P]),
@@ -296,6 +298,19 @@ def tm_subproblems(n: int, m: int, p: int, xbar, ybar, table=None, stream=None):
 def tm_read_status(status, stream=None) -> int:
     """Synchronises the stream and returns the device status word (0 = ok)."""
     return int(load().tm_read_status(_dev(status, "status"), _stream(stream)))
+
+
+PHASES = ("search", "barrier1", "select", "barrier2", "merge", "total")
+
+
+def tm_merge_phase_times(workspace, n: int, m: int, cfg, stream=None) -> dict:
+    """Phase times (microseconds) of the last traced fused launch of tm_merge
+    on `workspace` (cfg with trace = 1, same n, m, cfg)."""
+    out = (ctypes.c_double * 6)()
+    code = load().tm_merge_phase_times(_dev(workspace, "workspace", (torch.uint8,)), n, m, _cfg(cfg),
+                                       ctypes.cast(out, ctypes.c_void_p), _stream(stream))
+    _check(code, "tm_merge_phase_times")
+    return dict(zip(PHASES, list(out)))
 
 
 def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream=None):

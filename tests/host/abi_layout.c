@@ -21,6 +21,8 @@ int main(void)
     FIELD(tm_config, test_drop_tile);
     FIELD(tm_config, unfused);
     FIELD(tm_config, partition);
+    FIELD(tm_config, payload_bytes);
+    FIELD(tm_config, trace);
     FIELD(tm_config, reserved);
     printf("sizeof %zu\n", sizeof(tm_config));
     return 0;

@@ -157,6 +157,17 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
     # the allocation-free merge: lengths, key type, alignment
     assert lib.tm_merge_noalloc(0, k8, v4, -1, k8, v4, 1, k8, v4, None, None, None) == INV
     assert lib.tm_merge_noalloc(9, k8, v4, 1, k8, v4, 1, k8, v4, None, None, None) == UNS
+    # phase times need a traced configuration and an output array
+    out6 = (ctypes.c_double * 6)()
+    assert lib.tm_merge_phase_times(P(256), 10, 10, None, ctypes.cast(out6, ctypes.c_void_p), None) == INV
+    ct = tm.TmConfig(trace=1)
+    assert lib.tm_merge_phase_times(P(256), 10, 10, ctypes.byref(ct), None, None) == INV
+    assert lib.tm_merge_phase_times(P(8), 10, 10, ctypes.byref(ct), ctypes.cast(out6, ctypes.c_void_p), None) == INV
+    # 8-byte payload words are not taken by these calls yet
+    c8 = tm.TmConfig(payload_bytes=8)
+    assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(c8), None) == UNS
+    c3 = tm.TmConfig(payload_bytes=3)
+    assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(c3), None) == UNS
     # configurations tm_merge refuses are refused here too (before any device work)
     for bad in ({"partition": tm.TM_PARTITION_DIAGONALS}, {"partition": 7}, {"threads": 64}, {"threads": 384}):
         c = tm.TmConfig(**bad)

@@ -277,3 +277,24 @@ def test_large_merge_full_size(dist, skewed):
     K, V = oracle.merge_two_pointer(hA, hAv, hB, hBv)
     assert first_mismatch(ck, K) is None, f"key mismatch at {first_mismatch(ck, K)}"
     assert first_mismatch(cv, V) is None, f"payload mismatch at {first_mismatch(cv, V)}"
+
+
+def test_traced_fused_launch_gives_phase_times_and_the_same_merge():
+    """cfg trace = 1 records per-CTA phase stamps of the fused launch; the
+    merge is unchanged and the phases add up to the kernel's time."""
+    A, Av, B, Bv = W.single_merge_1m("cpu")
+    cfg = {"p": 1024, "trace": 1}
+    gpu_merge_check("u32", A, Av, B, Bv, cfg=cfg)
+    n, m = A.numel(), B.numel()
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), DEV)
+    d = [t.to(DEV) for t in (A, Av, B, Bv)]
+    tm.tm_merge("u32", *d, None, None, ws, cfg=cfg)
+    ph = tm.tm_merge_phase_times(ws, n, m, cfg)
+    assert all(v >= 0 for v in ph.values())
+    assert ph["merge"] > 0 and ph["search"] > 0
+    assert abs(sum(ph[k] for k in tm.PHASES[:5]) - ph["total"]) < 1e-6 * max(1.0, ph["total"]) + 1e-3
+    # a separate-launch call records no trace
+    cfg_u = {"p": 1024, "trace": 1, "unfused": 1}
+    tm.tm_merge("u32", *d, None, None, ws, cfg=cfg_u)
+    with pytest.raises(tm.TmError):
+        tm.tm_merge_phase_times(ws, n, m, cfg_u)
