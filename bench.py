@@ -68,7 +68,8 @@ def measured_peaks():
 # stand only while these files are unchanged.
 KERNEL_SOURCES = {
     "merge_engine_kernel": ["tm_engine.cuh", "tm_engine_launch.cuh", "tm_engine_i32.cu", "tm_engine_u32.cu",
-                            "tm_engine_u64.cu", "tm_engine_f32.cu", "tm_common.cuh", "tm_host.h"],
+                            "tm_engine_u64.cu", "tm_engine_f32.cu", "tm_engine_i32_v64.cu", "tm_engine_u32_v64.cu",
+                            "tm_engine_u64_v64.cu", "tm_engine_f32_v64.cu", "tm_common.cuh", "tm_host.h"],
 }
 
 
@@ -380,6 +381,9 @@ def compact_forms(forms: dict, peak_gbs: float) -> dict:
                           "search_speedup_pla_only": _r(f.get("search_speedup_pla_only")),
                           "fallbacks": g(g(f, "learned"), "fallbacks"), "bit_identical": f.get("bit_identical"),
                           "cpu": _r(g(g(f, "cpu_baseline"), "value"))}
+    f = forms.get("payload64")
+    if isinstance(f, dict) and "error" not in f:
+        out["payload64"] = {"value": _r(f.get("value")), "ms": _r(f.get("ms")), "frac_of_hbm": _r(f.get("frac_of_hbm"))}
     f = forms.get("partition_ablation")
     if isinstance(f, dict) and "error" not in f:
         out["partition_ablation"] = {"equal_output_over_blocks": _r(f.get("equal_output_over_blocks"))}
@@ -548,6 +552,38 @@ def bench_keys_only(dev, steps: int = 20):
         out[dist] = {"ms": ms, "value": (n + m) / (ms / 1e3), "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0]}
         del A, B, C, ws
         torch.cuda.empty_cache()
+    return out
+
+
+def bench_payload64(dev, steps: int = 10):
+    """8-byte payload words (tm_config.payload_bytes = 8): n = m = 2**28 int32
+    keys uniform over int32 with 64-bit payloads, tm_merge through the C ABI,
+    median of `steps` calls; 24 B per output element (4 + 8 read, 4 + 8
+    written)."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    A, Av, B, Bv = W.large_merge("uniform_full", False, dev)
+    Aw, Bw = W.widen_payload(Av), W.widen_payload(Bv)
+    del Av, Bv
+    n, m = A.numel(), B.numel()
+    C = torch.empty(n + m, dtype=torch.int32, device=dev)
+    Cw = torch.empty(n + m, dtype=torch.int64, device=dev)
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m), dev)
+    tm.tm_merge("i32", A, Aw, B, Bw, C, Cw, ws)
+    ts = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tm.tm_merge("i32", A, Aw, B, Bw, C, Cw, ws)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    assert tm.tm_read_status(ws) == 0
+    ms = float(np.median(ts))
+    gbs = (n + m) * 24 / (ms / 1e3) / 1e9
+    out = {"workload": "n = m = 2^28 int32 keys (uniform over int32) + 8-byte payloads", "unit": UNIT,
+           "ms": ms, "value": (n + m) / (ms / 1e3), "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0]}
+    del A, Aw, B, Bw, C, Cw, ws
+    torch.cuda.empty_cache()
     return out
 
 
@@ -810,7 +846,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
     ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys",
-                                                   "partition"],
+                                                   "partition", "payload64"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
     ap.add_argument("--pairs", type=int, default=65536, help="batched form: pairs (profiling)")
@@ -844,6 +880,8 @@ def main():
             out = bench_keys_only(dev)
         elif args.form == "partition":
             out = bench_partition(dev)
+        elif args.form == "payload64":
+            out = bench_payload64(dev)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)
@@ -1045,7 +1083,7 @@ def main():
         torch.cuda.empty_cache()
         forms = {"merge_1m_p1024": bench_small_merge(dev), "batched": bench_batched(dev),
                  "merge_sort": bench_sort(dev), "keys_only": bench_keys_only(dev),
-                 "partition_ablation": bench_partition(dev)}
+                 "payload64": bench_payload64(dev), "partition_ablation": bench_partition(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

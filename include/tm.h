@@ -34,6 +34,11 @@
  *    only the device can see (a subproblem larger than its staging buffer, a
  *    bounded wait that gave up) are written to a device status word that
  *    tm_read_status() returns; kernels never trap.
+ *  - Payload width: payloads are 4-byte words unless cfg->payload_bytes = 8
+ *    selects 8-byte words (tm_merge, tm_merge_tiles, tm_merge_batched,
+ *    tm_merge_sort and the autotuners; the payload pointers keep their
+ *    uint32_t* type and must then be 8-byte aligned).  tm_merge_noalloc and
+ *    the learned calls take 4-byte payloads only.
  *  - Keys-only merges: every merge and sort call accepts NULL for all of its
  *    payload pointers (a_vals, b_vals and c_vals together; vals and tmp_vals
  *    together for the sort) and then moves keys only (half the bytes for
@@ -307,9 +312,12 @@ TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64
  * configuration -- tile {1024, 2048, 4096} x threads {128, 256} x stages
  * {3, 4}, diagonal in-CTA split, skipping those whose workspace exceeds
  * workspace_bytes -- timed with CUDA events on `stream`, and keeps the
- * fastest for later calls with cfg NULL on the same key type and size
- * (power-of-two bucket of the element count).  Synchronises the stream.
- * *best receives the chosen configuration. */
+ * fastest for later calls with cfg NULL (or setting only payload_bytes) on
+ * the same key type, payload width and size (power-of-two bucket of the
+ * element count).  Synchronises the stream.  On input best->payload_bytes (0
+ * or 4: 4-byte payloads, 8: 8-byte payloads; best NULL: 4) selects the
+ * payload width of the trials; on return *best holds the chosen
+ * configuration. */
 TM_API tm_status tm_autotune_batched(tm_key_type kt, int64_t num_pairs,
                                      const int64_t* a_offsets, const void* a_keys, const uint32_t* a_vals,
                                      int64_t total_a,

@@ -377,8 +377,8 @@ static BatchedWs batched_ws_layout(void* base, int64_t pairs, int64_t total, int
 // Runs search, plan and the engine for a pair set; `ws` laid out as above.
 template <typename K>
 static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_a, int64_t total_b,
-                           const K* A, const uint32_t* Av, const K* B, const uint32_t* Bv,
-                           K* C, uint32_t* Cv, int64_t tile, int64_t known_items,
+                           const K* A, const void* Av, const K* B, const void* Bv,
+                           K* C, void* Cv, int vbytes, int64_t tile, int64_t known_items,
                            const tm_config* cfg, cudaStream_t s) {
     const int64_t total = total_a + total_b;
     PairBases pb{w.search_base, w.rank_base, w.item_base, w.cta_pair};
@@ -413,6 +413,7 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
     a.A = A; a.Av = Av; a.lenA = total_a;
     a.B = B; a.Bv = Bv; a.lenB = total_b;
     a.C = C; a.Cv = Cv;
+    a.vbytes = vbytes;
     a.cap = (int)(tile + 2);
     if (a.items_bound == 0) return TM_OK;
     return launch_engine<K>(a, cfg, s);
@@ -431,7 +432,7 @@ static tm_status batched_typed(int64_t pairs, const int64_t* a_off, const void* 
     ps.num_pairs = pairs; ps.a_off = a_off; ps.b_off = b_off;
     return run_pairs<K>(ps, w, total_a, total_b, static_cast<const K*>(a_keys), a_vals,
                         static_cast<const K*>(b_keys), b_vals, static_cast<K*>(c_keys), c_vals,
-                        tile, -1, cfg, s);
+                        payload_size(cfg), tile, -1, cfg, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -455,12 +456,12 @@ constexpr int kSortRun = 1024;
 constexpr int kSortThreads = 128;
 constexpr int kSortVT = 9;
 
-template <typename K>
+template <typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads)
-run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K* __restrict__ out_k,
-                uint32_t* __restrict__ out_v, int64_t n) {
+run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __restrict__ out_k,
+                V* __restrict__ out_v, int64_t n) {
     __shared__ K sk[kSortRun + 1];                    // + 1: the merge step reads one past a run
-    __shared__ uint32_t sv[kSortRun];
+    __shared__ V sv[kSortRun];
     const int t = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * kSortRun;
     const int len = (int)(n - base < kSortRun ? n - base : kSortRun);
@@ -472,14 +473,14 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
     // blocked registers: thread t holds elements [kSortVT*t, kSortVT*(t+1)); missing ones
     // (past len) are marked invalid and sort to the end
     K k[kSortVT];
-    uint32_t v[kSortVT];
+    V v[kSortVT];
     bool ok[kSortVT];
 #pragma unroll
     for (int q = 0; q < kSortVT; ++q) {
         const int i = t * kSortVT + q;
         ok[q] = i < len;
         k[q] = K();
-        v[q] = 0u;
+        v[q] = V();
         if (ok[q]) { k[q] = sk[i]; v[q] = sv[i]; }
     }
     // stable odd-even transposition sort of kSortVT (invalid elements are largest)
@@ -490,7 +491,7 @@ run_sort_kernel(const K* __restrict__ in_k, const uint32_t* __restrict__ in_v, K
             const bool swap = ok[q + 1] && (!ok[q] || k[q + 1] < k[q]);
             if (swap) {
                 const K tk = k[q]; k[q] = k[q + 1]; k[q + 1] = tk;
-                const uint32_t tv = v[q]; v[q] = v[q + 1]; v[q + 1] = tv;
+                const V tv = v[q]; v[q] = v[q + 1]; v[q + 1] = tv;
                 const bool to = ok[q]; ok[q] = ok[q + 1]; ok[q + 1] = to;
             }
         }
@@ -584,15 +585,15 @@ static BatchedWs sort_ws_layout(void* base, int64_t n, int64_t tile) {
     return ws_layout(base, 0, ranks, items, 0);
 }
 
-template <typename K>
-static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
-                            void* ws, const tm_config* cfg, cudaStream_t s) {
+template <typename K, typename V>
+static tm_status sort_typed_v(void* keys, void* vals, int64_t n, void* tmp_keys, void* tmp_vals,
+                              void* ws, const tm_config* cfg, cudaStream_t s) {
     const int64_t tile = tile_of(cfg);
     BatchedWs w = sort_ws_layout(ws, n, tile);
     if (const cudaError_t e_ = cudaMemsetAsync(w.control, 0, 16, s); e_ != cudaSuccess) return cuda_failed(e_);
     if (n <= 1) return TM_OK;
     K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
-    uint32_t* bufv[2] = {vals, tmp_vals};
+    V* bufv[2] = {static_cast<V*>(vals), static_cast<V*>(tmp_vals)};
     // number of merge rounds decides where the run formation writes, so that
     // the last round lands in (keys, vals)
     int rounds = 0;
@@ -600,18 +601,25 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
     int src = (rounds % 2 == 0) ? 0 : 1;
     const int64_t runs = (n + kSortRun - 1) / kSortRun;
     if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
-    run_sort_kernel<K><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
+    run_sort_kernel<K, V><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
     if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
     for (int64_t run = kSortRun; run < n; run *= 2) {
         int64_t items = 0;
         const PairSet ps = sort_round(n, run, tile, &items);
         const int dst = src ^ 1;
         tm_status st = run_pairs<K>(ps, w, n, n, bufk[src], bufv[src], bufk[src], bufv[src],
-                                    bufk[dst], bufv[dst], tile, items, cfg, s);
+                                    bufk[dst], bufv[dst], (int)sizeof(V), tile, items, cfg, s);
         if (st != TM_OK) return st;
         src = dst;
     }
     return TM_OK;
+}
+
+template <typename K>
+static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
+                            void* ws, const tm_config* cfg, cudaStream_t s) {
+    if (payload_size(cfg) == 8) return sort_typed_v<K, uint64_t>(keys, vals, n, tmp_keys, tmp_vals, ws, cfg, s);
+    return sort_typed_v<K, uint32_t>(keys, vals, n, tmp_keys, tmp_vals, ws, cfg, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -620,17 +628,26 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
 // ---------------------------------------------------------------------------
 
 struct TuneKey {
-    int op, kt, log2_total;
-    bool operator<(const TuneKey& o) const { return std::tie(op, kt, log2_total) < std::tie(o.op, o.kt, o.log2_total); }
+    int op, kt, vbytes, log2_total;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(op, kt, vbytes, log2_total) < std::tie(o.op, o.kt, o.vbytes, o.log2_total);
+    }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, tm_config> g_tune;
 
 static int log2_bucket(int64_t x) { int b = 0; while ((int64_t(1) << (b + 1)) <= x) ++b; return b; }
 
-static bool tuned_config(int op, tm_key_type kt, int64_t total, tm_config* out) {
+// The autotuned configuration for a call whose cfg is NULL or sets nothing
+// but the payload width.
+static bool tuned_config(int op, tm_key_type kt, int64_t total, const tm_config* cfg, tm_config* out) {
+    if (cfg) {
+        tm_config d{};
+        d.payload_bytes = cfg->payload_bytes;
+        if (std::memcmp(&d, cfg, sizeof(tm_config)) != 0) return false;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune.find(TuneKey{op, (int)kt, log2_bucket(total)});
+    auto it = g_tune.find(TuneKey{op, (int)kt, payload_size(cfg), log2_bucket(total)});
     if (it == g_tune.end()) return false;
     *out = it->second;
     return true;
@@ -643,13 +660,14 @@ using namespace pmerge;
 namespace {
 tm_status check_batched(tm_key_type kt, int64_t pairs, const int64_t* a_off, const void* a_keys,
                         const uint32_t* a_vals, int64_t total_a, const int64_t* b_off, const void* b_keys,
-                        const uint32_t* b_vals, int64_t total_b, void* c_keys, uint32_t* c_vals) {
+                        const uint32_t* b_vals, int64_t total_b, void* c_keys, uint32_t* c_vals, int vsize) {
     if (pairs < 0 || total_a < 0 || total_b < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || vsize < 0) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (pairs > 0 && (!aligned(a_off, 8) || !aligned(b_off, 8))) return TM_ERR_INVALID;
     if ((total_a > 0 && !aligned(a_keys, E)) || (total_b > 0 && !aligned(b_keys, E)) ||
-        (total_a + total_b > 0 && !aligned(c_keys, E)) || !payloads_ok(total_a, a_vals, total_b, b_vals, c_vals))
+        (total_a + total_b > 0 && !aligned(c_keys, E)) ||
+        !payloads_ok(total_a, a_vals, total_b, b_vals, c_vals, vsize))
         return TM_ERR_INVALID;
     return TM_OK;
 }
@@ -681,11 +699,10 @@ tm_status tm_merge_batched(tm_key_type kt, int64_t num_pairs,
                            void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
                            const tm_config* cfg, tm_stream_t stream) {
     tm_status st = check_batched(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
-                                 total_b, c_keys, c_vals);
+                                 total_b, c_keys, c_vals, payload_size(cfg));
     if (st != TM_OK) return st;
-    if (payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
     tm_config tuned;
-    if (!cfg && tuned_config(1, kt, total_a + total_b, &tuned)) cfg = &tuned;
+    if (tuned_config(1, kt, total_a + total_b, cfg, &tuned)) cfg = &tuned;
     if (!workspace || !aligned(workspace, 256) ||
         workspace_bytes < tm_merge_batched_workspace_size(num_pairs, total_a, total_b, cfg))
         return TM_ERR_WORKSPACE;
@@ -701,13 +718,14 @@ size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg) {
 tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
                         void* workspace, size_t workspace_bytes, const tm_config* cfg, tm_stream_t stream) {
     if (n < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
+    const int vs = payload_size(cfg);
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || vs < 0) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (n > 0 && (!aligned(keys, E) || !aligned(tmp_keys, E) ||
-                  ((vals || tmp_vals) && (!aligned(vals, 4) || !aligned(tmp_vals, 4)))))
+                  ((vals || tmp_vals) && (!aligned(vals, vs) || !aligned(tmp_vals, vs)))))
         return TM_ERR_INVALID;                      // vals and tmp_vals both NULL: keys only
     tm_config tuned;
-    if (!cfg && tuned_config(2, kt, n, &tuned)) cfg = &tuned;
+    if (tuned_config(2, kt, n, cfg, &tuned)) cfg = &tuned;
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < tm_merge_sort_workspace_size(n, cfg))
         return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -746,8 +764,8 @@ std::vector<tm_config> tune_candidates() {
 }
 
 template <typename Run>
-tm_status tune(int op, tm_key_type kt, int64_t total, size_t ws_have, size_t (*ws_need)(const tm_config*),
-               Run run, tm_config* best_out, cudaStream_t s) {
+tm_status tune(int op, tm_key_type kt, int vbytes, int64_t total, size_t ws_have,
+               size_t (*ws_need)(const tm_config*), Run run, tm_config* best_out, cudaStream_t s) {
     cudaEvent_t e0, e1;
     if (const cudaError_t e = cudaEventCreate(&e0); e != cudaSuccess) return cuda_failed(e);
     if (const cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
@@ -756,7 +774,8 @@ tm_status tune(int op, tm_key_type kt, int64_t total, size_t ws_have, size_t (*w
     }
     float best_ms = -1.f;
     tm_config best{};
-    for (const tm_config& c : tune_candidates()) {
+    for (tm_config c : tune_candidates()) {
+        c.payload_bytes = vbytes;
         if (ws_need(&c) > ws_have) continue;
         if (run(&c) != TM_OK) continue;                   // warm-up (and support check)
         cudaEventRecord(e0, s);
@@ -772,7 +791,7 @@ tm_status tune(int op, tm_key_type kt, int64_t total, size_t ws_have, size_t (*w
     if (best_ms < 0.f) return TM_ERR_UNSUPPORTED;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[TuneKey{op, (int)kt, log2_bucket(total)}] = best;
+        g_tune[TuneKey{op, (int)kt, vbytes, log2_bucket(total)}] = best;
     }
     if (best_out) *best_out = best;
     return TM_OK;
@@ -791,8 +810,9 @@ tm_status tm_autotune_batched(tm_key_type kt, int64_t num_pairs,
                               const int64_t* b_offsets, const void* b_keys, const uint32_t* b_vals, int64_t total_b,
                               void* c_keys, uint32_t* c_vals, void* workspace, size_t workspace_bytes,
                               tm_config* best, tm_stream_t stream) {
+    const int vb = best ? payload_size(best) : 4;      // *best on input: the payload width of the trials
     tm_status st = check_batched(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
-                                 total_b, c_keys, c_vals);
+                                 total_b, c_keys, c_vals, vb);
     if (st != TM_OK) return st;
     if (!workspace || !aligned(workspace, 256)) return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -801,18 +821,19 @@ tm_status tm_autotune_batched(tm_key_type kt, int64_t num_pairs,
         return batched_dispatch(kt, num_pairs, a_offsets, a_keys, a_vals, total_a, b_offsets, b_keys, b_vals,
                                 total_b, c_keys, c_vals, workspace, c, s);
     };
-    return tune(1, kt, total_a + total_b, workspace_bytes, batched_ws_need, run, best, s);
+    return tune(1, kt, vb, total_a + total_b, workspace_bytes, batched_ws_need, run, best, s);
 }
 
 tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t* src_vals, int64_t n,
                            void* keys, uint32_t* vals, void* tmp_keys, uint32_t* tmp_vals,
                            void* workspace, size_t workspace_bytes, tm_config* best, tm_stream_t stream) {
     if (n < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32) return TM_ERR_UNSUPPORTED;
+    const int vb = best ? payload_size(best) : 4;      // *best on input: the payload width of the trials
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || vb < 0) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (n > 0 && (!aligned(src_keys, E) || !aligned(keys, E) || !aligned(tmp_keys, E) ||
                   ((src_vals || vals || tmp_vals) &&
-                   (!aligned(src_vals, 4) || !aligned(vals, 4) || !aligned(tmp_vals, 4)))))
+                   (!aligned(src_vals, vb) || !aligned(vals, vb) || !aligned(tmp_vals, vb)))))
         return TM_ERR_INVALID;
     if (!workspace || !aligned(workspace, 256)) return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -822,11 +843,11 @@ tm_status tm_autotune_sort(tm_key_type kt, const void* src_keys, const uint32_t*
     auto run = [&](const tm_config* c) -> tm_status {
         cudaError_t e = cudaMemcpyAsync(keys, src_keys, (size_t)n * E, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess && vals)                 // keys-only sort: no payloads to copy
-            e = cudaMemcpyAsync(vals, src_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+            e = cudaMemcpyAsync(vals, src_vals, (size_t)n * vb, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_failed(e);
         return tm_merge_sort(kt, keys, vals, n, tmp_keys, tmp_vals, workspace, workspace_bytes, c, stream);
     };
-    return tune(2, kt, n, workspace_bytes, sort_ws_need, run, best, s);
+    return tune(2, kt, vb, n, workspace_bytes, sort_ws_need, run, best, s);
 }
 
 int tm_autotune_clear(void) {

@@ -68,6 +68,63 @@ __host__ __device__ __forceinline__ I first_block_at_or_after(I len, I p, I k) {
     return (block_start(len, p, j) == k) ? j : j + 1;
 }
 
+// Division by an invariant divisor (Lemire, Kaser and Kurz, "Faster
+// remainder by direct computation", 2019): for x, d < 2^32 and d > 1,
+// floor(x / d) is the high 64 bits of the 128-bit product c * x with
+// c = ceil(2^64 / d).  d = 1 returns x.
+struct FastDiv32 {
+    uint64_t c;
+    uint32_t d;
+    __host__ __device__ FastDiv32() : c(0), d(1) {}
+    __host__ __device__ explicit FastDiv32(uint32_t dd) : c(dd > 1 ? ~0ull / dd + 1 : 0), d(dd) {}
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t x) const {
+        if (d <= 1) return x;
+#ifdef __CUDA_ARCH__
+        return (uint32_t)__umul64hi(c, (uint64_t)x);
+#else
+        return (uint32_t)(((unsigned __int128)c * x) >> 64);
+#endif
+    }
+};
+
+// The block decomposition of Section 2 for len + p < 2^32, with its
+// parameters computed once: q = floor(len / p), r = len mod p (the first r
+// blocks one longer), head = r (q + 1) = the end of the longer blocks.
+// Same values as block_start / block_of / first_block_at_or_after.
+struct Blocks32 {
+    uint32_t len, p, q, r, head;
+    FastDiv32 dq1, dq;                              // division by q + 1 and by q
+    __host__ __device__ Blocks32() : len(0), p(1), q(0), r(0), head(0) {}
+    __host__ __device__ Blocks32(uint32_t len_, uint32_t p_)
+        : len(len_), p(p_), q(len_ / p_), r(len_ % p_), head((len_ % p_) * (len_ / p_ + 1)),
+          dq1(len_ / p_ + 1), dq(len_ / p_) {}
+    // x_i for 0 <= i <= p
+    __host__ __device__ __forceinline__ int64_t start(int64_t i) const {
+        const uint32_t u = (uint32_t)i;
+        return (int64_t)(u < r ? u * (q + 1) : u * q + r);
+    }
+    // block holding index k (0 <= k <= len); k = len -> p
+    __host__ __device__ __forceinline__ int64_t of(int64_t k) const {
+        const uint32_t u = (uint32_t)k;
+        if (u >= len) return p;
+        return (int64_t)(u < head ? dq1.div(u) : dq.div(u - head) + r);
+    }
+    // smallest block index whose start is >= k (0 <= k <= len)
+    __host__ __device__ __forceinline__ int64_t first_at_or_after(int64_t k) const {
+        if ((uint32_t)k >= len) return len < p ? len : p;
+        const int64_t j = of(k);
+        return start(j) == k ? j : j + 1;
+    }
+};
+
+// The same decomposition through the general functions above (any length).
+template <typename I>
+struct BlocksOf {
+    I len, p;
+    __host__ __device__ __forceinline__ I start(I i) const { return block_start<I>(len, p, i); }
+    __host__ __device__ __forceinline__ I first_at_or_after(I k) const { return first_block_at_or_after<I>(len, p, k); }
+};
+
 // ---------------------------------------------------------------------------
 // Rank primitives (Section 2)
 // ---------------------------------------------------------------------------
@@ -131,27 +188,34 @@ __device__ __forceinline__ int rank_high_smem(const K* X, int len, K x) {
 // mirror.  Returns the A range [a0, a1), B range [b0, b1); the output starts
 // at a0 + b0.
 
-template <typename I, typename LoadXbar, typename LoadYbar>
-__device__ __forceinline__ void subproblem_of(bool a_side, I pe, I n, I m, I p,
-                                              LoadXbar xbar, LoadYbar ybar,
-                                              I& a0, I& a1, I& b0, I& b1) {
+// bA, bB: the block decompositions of A and B (start(i), first_at_or_after(k)).
+template <typename I, typename BA, typename BB, typename LoadXbar, typename LoadYbar>
+__host__ __device__ __forceinline__ void subproblem_in(bool a_side, I pe, I p, const BA& bA, const BB& bB,
+                                                       LoadXbar xbar, LoadYbar ybar, I& a0, I& a1, I& b0, I& b1) {
     if (a_side) {
-        I xi = block_start(n, p, pe), xi1 = block_start(n, p, pe + 1);
+        I xi = bA.start(pe), xi1 = bA.start(pe + 1);
         I xb = xbar(pe), xb1 = xbar(pe + 1);
         a0 = xi; b0 = xb;
-        I jn = first_block_at_or_after(m, p, xb);
-        I yjn = block_start(m, p, jn);
+        I jn = bB.first_at_or_after(xb);
+        I yjn = bB.start(jn);
         if (jn < p && yjn < xb1) { a1 = ybar(jn); b1 = yjn; }
         else                     { a1 = xi1;      b1 = xb1; }
     } else {
-        I yj = block_start(m, p, pe), yj1 = block_start(m, p, pe + 1);
+        I yj = bB.start(pe), yj1 = bB.start(pe + 1);
         I yb = ybar(pe), yb1 = ybar(pe + 1);
         b0 = yj; a0 = yb;
-        I in = first_block_at_or_after(n, p, yb);
-        I xin = block_start(n, p, in);
+        I in = bA.first_at_or_after(yb);
+        I xin = bA.start(in);
         if (in < p && xin < yb1) { b1 = xbar(in); a1 = xin; }
         else                     { b1 = yj1;      a1 = yb1; }
     }
+}
+
+template <typename I, typename LoadXbar, typename LoadYbar>
+__host__ __device__ __forceinline__ void subproblem_of(bool a_side, I pe, I n, I m, I p,
+                                                       LoadXbar xbar, LoadYbar ybar,
+                                                       I& a0, I& a1, I& b0, I& b1) {
+    subproblem_in<I>(a_side, pe, p, BlocksOf<I>{n, p}, BlocksOf<I>{m, p}, xbar, ybar, a0, a1, b0, b1);
 }
 
 // ---------------------------------------------------------------------------

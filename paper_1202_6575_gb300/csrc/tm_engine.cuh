@@ -98,10 +98,10 @@ __device__ __forceinline__ void rank_pair_smem(const K* X, int lenX, K x, int& r
 // Serial stable merge of sA[ia0..ia1) and sB[ib0..ib1) into sC from ia0 + ib0
 // (B taken only when strictly smaller).  Reads at most one element past a
 // range end, which lies inside the padded stage region.
-template <typename K>
-__device__ __forceinline__ void merge_run(const K* sAk, const uint32_t* sAv, int ia0, int ia1,
-                                          const K* sBk, const uint32_t* sBv, int ib0, int ib1,
-                                          K* sCk, uint32_t* sCv) {
+template <typename K, typename V>
+__device__ __forceinline__ void merge_run(const K* sAk, const V* sAv, int ia0, int ia1,
+                                          const K* sBk, const V* sBv, int ib0, int ib1,
+                                          K* sCk, V* sCv) {
     int i = ia0, j = ib0, o = ia0 + ib0;
     const int oend = ia1 + ib1;
     K ka = sAk[i];
@@ -111,7 +111,7 @@ __device__ __forceinline__ void merge_run(const K* sAk, const uint32_t* sAv, int
         const bool takeB = (j < ib1) && ((i >= ia1) || (kb < ka));
         const int idx = takeB ? j : i;
         const K* ks = takeB ? sBk : sAk;
-        const uint32_t* vs = takeB ? sBv : sAv;
+        const V* vs = takeB ? sBv : sAv;
         sCk[o] = takeB ? kb : ka;
         sCv[o] = vs[idx];
         const K nxt = ks[idx + 1];
@@ -140,7 +140,8 @@ __device__ __forceinline__ int corank_smem(const K* sA, int nA, const K* sB, int
 // A piece at the start of a region, B piece at a 16-byte boundary after it;
 // each piece sits at the misalignment of its global source so that the
 // aligned middle is one bulk copy.  Per output buffer: keys | payloads, at
-// the misalignment of the global destination.
+// the misalignment of the global destination.  A keys-only launch (vsize 0)
+// has no payload regions, so more CTAs fit on an SM.
 
 struct EngineLayout {
     uint32_t stage_bytes, keys_off, vals_off;   // within a stage
@@ -151,15 +152,16 @@ struct EngineLayout {
 
 __host__ __device__ inline uint32_t ru128(uint32_t x) { return (x + 127u) & ~127u; }
 
-__host__ __device__ inline EngineLayout make_engine_layout(int cap, int ksize, int T, int s_in, int s_out) {
+__host__ __device__ inline EngineLayout make_engine_layout(int cap, int ksize, int vsize, int T, int s_in,
+                                                          int s_out) {
     EngineLayout L;
     uint32_t kreg = ru128((uint32_t)cap * ksize + 96);
-    uint32_t vreg = ru128((uint32_t)cap * 4 + 96);
+    uint32_t vreg = vsize ? ru128((uint32_t)cap * vsize + 96) : 0u;
     L.keys_off = 128;
     L.vals_off = 128 + kreg;
     L.stage_bytes = 128 + kreg + vreg;
     L.out_vals_off = ru128((uint32_t)cap * ksize + 16);
-    L.out_bytes = L.out_vals_off + ru128((uint32_t)cap * 4 + 16);
+    L.out_bytes = L.out_vals_off + (vsize ? ru128((uint32_t)cap * vsize + 16) : 0u);
     L.bars_off = 0;                                   // 2 * s_in mbarriers (<= 128 B)
     L.split_off = 128;
     uint32_t o = 128 + ru128(8u * (T + 1));
@@ -187,9 +189,10 @@ struct EngineArgs {
     int64_t items_bound;           // upper bound of the record count (host side, for sizing)
     unsigned long long* queue;     // work-queue counter, zero at launch
     int32_t* status;
-    const void* A; const uint32_t* Av; int64_t lenA;   // arrays the descriptors index
-    const void* B; const uint32_t* Bv; int64_t lenB;
-    void* C; uint32_t* Cv;
+    const void* A; const void* Av; int64_t lenA;       // arrays the descriptors index; payload
+    const void* B; const void* Bv; int64_t lenB;       // words of vbytes bytes (NULL: keys only)
+    void* C; void* Cv;
+    int vbytes;                                         // 4 or 8
     int cap;                       // max nA + nB of any tile
     int grab;                      // records per queue grab (<= 32)
     uint64_t wait_ns;              // limit of every mbarrier wait
@@ -204,10 +207,12 @@ struct EngineArgs {
     int64_t* fy;
     int64_t fp;
     unsigned int* gbar;
+    Blocks32 fbA, fbB;             // the block decompositions of A and B into fp blocks (n + fp < 2^32)
     // Profiling (nullptr = off): trace[0] = gridDim.x, then kTraceSlots
-    // %globaltimer stamps per CTA from trace[kTraceSlots]: kernel entry,
-    // searches done, first barrier passed, selection done, second barrier
-    // passed, merges done.
+    // words per CTA from trace[kTraceSlots]: %globaltimer at kernel entry,
+    // searches done, barrier passed, first subproblems selected (twice: the
+    // launch has no second barrier), merges done, first tile landed; then
+    // the number of tiles the CTA merged.
     uint64_t* trace;
 };
 
@@ -307,26 +312,34 @@ __device__ __forceinline__ void plan_single_record(int64_t n, int64_t m, int64_t
 }
 
 // Rank of x in sorted X[0..len) by one warp: each round the 32 lanes probe
-// 32 positions splitting the candidate range [lo, hi] into 33 parts and the
-// ballot of "X[q-1] lies before x" (true on a prefix of the lanes, X being
-// sorted) keeps one part; ceil(log33(len + 1)) rounds instead of
-// ceil(log2(len + 1)) dependent probes.  HIGH: rank_high (elements <= x),
-// else rank_low (elements < x).  Every lane returns the rank.
+// 32 positions splitting the candidate range [lo, hi] into 33 parts, and
+// the count of probes that lie before x (X sorted: a prefix of the lanes)
+// keeps one part: ceil(log33(len + 1)) rounds of independent loads instead
+// of ceil(log2(len + 1)) dependent probes.  HIGH: rank_high (elements <= x),
+// else rank_low (elements < x).  Every lane returns the rank.  The part
+// boundaries q_r = lo + ceil(r w / 33) in 32-bit arithmetic: with
+// w = 33 u + v (0 <= v < 33), ceil(r w / 33) = r u + ceil(r v / 33), where
+// r v < 33^2 keeps the division small.  len < 2^32.
+__device__ __forceinline__ uint32_t part33(uint32_t r, uint32_t u, uint32_t v) {
+    return r * u + (r * v + 32u) / 33u;
+}
+
 template <bool HIGH, typename K>
-__device__ __forceinline__ int64_t warp_rank(const K* __restrict__ X, int64_t len, K x, int lane) {
-    int64_t lo = 0, hi = len;
+__device__ __forceinline__ int64_t warp_rank33(const K* __restrict__ X, uint32_t len, K x, int lane) {
+    uint32_t lo = 0, hi = len;
     while (hi > lo) {
-        const int64_t w = hi - lo;
-        const int64_t q = lo + (((int64_t)lane + 1) * w + 32) / 33;      // in (lo, hi]
-        const K v = __ldg(X + q - 1);
-        const bool before = HIGH ? !(x < v) : (v < x);
+        const uint32_t w = hi - lo, u = w / 33u, v = w - 33u * (w / 33u);
+        const uint32_t q = lo + part33((uint32_t)lane + 1u, u, v);     // in (lo, hi]
+        const K val = __ldg(X + q - 1);
+        const bool before = HIGH ? !(x < val) : (val < x);
         const int c = __popc(__ballot_sync(0xffffffffu, before));
-        const int64_t qlo = __shfl_sync(0xffffffffu, q, c > 0 ? c - 1 : 0);
-        const int64_t qhi = __shfl_sync(0xffffffffu, q, c < 32 ? c : 31);
-        lo = c > 0 ? qlo : lo;
-        hi = c < 32 ? qhi - 1 : hi;
+        // probes 1..c lie before x: the rank is in [q_c, q_{c+1} - 1]
+        const uint32_t qlo = c > 0 ? lo + part33((uint32_t)c, u, v) : lo;
+        const uint32_t qhi = c < 32 ? lo + part33((uint32_t)c + 1u, u, v) - 1u : hi;
+        lo = qlo;
+        hi = qhi;
     }
-    return lo;
+    return (int64_t)lo;
 }
 
 // Fused single merge, Steps 1-2: the 2p + 1 cross ranks, one warp per
@@ -341,32 +354,19 @@ __device__ __forceinline__ void fused_cross_ranks(const EngineArgs& g) {
     const int64_t stride = (int64_t)gridDim.x * wpc;
     for (int64_t t = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); t <= 2 * p; t += stride) {
         if (t < p) {
-            const int64_t yj = block_start<int64_t>(m, p, t);
-            const int64_t r = (yj < m) ? warp_rank<true, K>(A, n, __ldg(B + yj), lane) : n;
+            const int64_t yj = g.fbB.start(t);
+            const int64_t r = (yj < m) ? warp_rank33<true, K>(A, (uint32_t)n, __ldg(B + yj), lane) : n;
             if (lane == 0) g.fy[t] = r;
         } else if (t < 2 * p) {
             const int64_t i = t - p;
-            const int64_t xi = block_start<int64_t>(n, p, i);
-            const int64_t r = (xi < n) ? warp_rank<false, K>(B, m, __ldg(A + xi), lane) : m;
+            const int64_t xi = g.fbA.start(i);
+            const int64_t r = (xi < n) ? warp_rank33<false, K>(B, (uint32_t)m, __ldg(A + xi), lane) : m;
             if (lane == 0) g.fx[i] = r;
         } else if (lane == 0) {
             g.fx[p] = m;
             g.fy[p] = n;
         }
     }
-}
-
-// Fused single merge, Steps 3-4 selection: every block's record, strided over
-// the grid's threads, into g.desc (the ranks were written in this launch, so
-// they are read through L2: ld.global.cg).
-__device__ __forceinline__ void fused_plan(const EngineArgs& g) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const long long* fx = reinterpret_cast<const long long*>(g.fx);
-    const long long* fy = reinterpret_cast<const long long*>(g.fy);
-    auto xb = [&](int64_t i) { return (int64_t)__ldcg(fx + i); };
-    auto yb = [&](int64_t j) { return (int64_t)__ldcg(fy + j); };
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * g.fp; k += stride)
-        plan_single_record(g.lenA, g.lenB, g.fp, k, xb, yb, const_cast<TileDesc*>(g.desc));
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA resident).  bar counts
@@ -398,21 +398,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int k, 
     return passed != 0;
 }
 
-// A work item's record: from the plan kernel's array, or, in the fused
-// launch, from the array this launch wrote (read through L2).
-template <bool FUSED>
-__device__ __forceinline__ TileDesc engine_record(const EngineArgs& g, int64_t q) {
-    if constexpr (FUSED) {
-        const int4* src = reinterpret_cast<const int4*>(g.desc + q);
-        TileDesc d;
-        int4* dst = reinterpret_cast<int4*>(&d);
-        dst[0] = __ldcg(src); dst[1] = __ldcg(src + 1); dst[2] = __ldcg(src + 2);
-        return d;
-    } else {
-        return g.desc[q];
-    }
-}
-
 // In-CTA split of a staged tile among the consumer threads:
 //   kSplitBlocks   - the paper's rule again: T blocks per piece, cross ranks
 //                    of the block starts, 2T sub-subproblems, two per thread,
@@ -425,12 +410,97 @@ __device__ __forceinline__ TileDesc engine_record(const EngineArgs& g, int64_t q
 //                    stored from there.
 enum { kSplitBlocks = 0, kSplitDiagonal = 1 };
 
+// Stages one tile -- A[a0, a0+nA) and B[b0, b0+nB), output from c0 -- into
+// input stage k % S_IN (the k-th fill of the CTA) once the consumers have
+// freed it.  Lanes 0..3 copy the four pieces (A keys, A payloads, B keys, B
+// payloads) in parallel; lane 0 writes the header and arms the stage's
+// barrier.  Returns false when the wait for a free stage gave up
+// (TM_ERR_TIMEOUT set); a tile over its capacity sets TM_ERR_BOUNDS and is
+// skipped.  Advances k for every fill it takes.
+template <typename K, typename V, int LOG_T, int S_IN, int SPLIT>
+__device__ __forceinline__ bool stage_tile(const EngineArgs& g, uint8_t* smem, uint64_t* full, uint64_t* empty,
+                                           int lane, int& k, int64_t a0, int64_t b0, int64_t c0, int nA, int nB) {
+    if (nA + nB == 0) return true;
+    if (nA < 0 || nB < 0 || nA + nB > g.cap) {
+        if (lane == 0) set_status(g.status, TM_ERR_BOUNDS);
+        return true;
+    }
+    const int s = k % S_IN;
+    int free_ok = 1;
+    if (lane == 0 && k >= S_IN) free_ok = mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns) ? 1 : 0;
+    free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+    if (!free_ok) {
+        if (lane == 0) set_status(g.status, TM_ERR_TIMEOUT);
+        return false;
+    }
+    if (k == g.drop_fill) {                           // testing: this stage never becomes ready
+        ++k;
+        return true;
+    }
+    uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
+    // piece of this lane: 0 A keys, 1 A payloads, 2 B keys, 3 B payloads
+    const bool isB = lane >= 2, isV = (lane & 1) != 0;
+    const uint32_t E = isV ? (uint32_t)sizeof(V) : (uint32_t)sizeof(K);
+    const void* pbase = isB ? (isV ? g.Bv : g.B) : (isV ? g.Av : g.A);
+    // keys-only merge (no payload arrays): the payload pieces are empty
+    const int64_t plen = isB ? g.lenB : g.lenA, plo = isB ? b0 : a0;
+    const int64_t pcnt = (isV && g.Cv == nullptr) ? 0 : (isB ? nB : nA);
+    uint8_t* region = st + (isV ? g.lay.vals_off : g.lay.keys_off);
+    uint32_t dst_off = 0;
+    if (isB) {   // after the A piece of the same region, on a 16-byte boundary
+        const uintptr_t abase = reinterpret_cast<uintptr_t>(isV ? g.Av : g.A);
+        const uint32_t aoff = (uint32_t)((abase + (uintptr_t)a0 * E) & 15);
+        dst_off = (aoff + (uint32_t)nA * E + 31u) & ~15u;
+    }
+    uint32_t tx = 0, off = 0, inv = 0;
+    if (lane < 4) {
+        off = stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], tx, 0);
+        if (SPLIT == kSplitBlocks) {                  // inverses of q+1 and q per piece length
+            const uint32_t qn = (uint32_t)(isB ? nB : nA) >> LOG_T;
+            inv = inv31(isV ? qn : qn + 1);
+        }
+    }
+    tx += __shfl_xor_sync(0xffffffffu, tx, 1);
+    tx += __shfl_xor_sync(0xffffffffu, tx, 2);
+    const uint32_t oKA = __shfl_sync(0xffffffffu, off, 0), oVA = __shfl_sync(0xffffffffu, off, 1);
+    const uint32_t oKB = __shfl_sync(0xffffffffu, off, 2), oVB = __shfl_sync(0xffffffffu, off, 3);
+    const uint32_t mA1 = __shfl_sync(0xffffffffu, inv, 0), mA0 = __shfl_sync(0xffffffffu, inv, 1);
+    const uint32_t mB1 = __shfl_sync(0xffffffffu, inv, 2), mB0 = __shfl_sync(0xffffffffu, inv, 3);
+    __syncwarp();                                     // plain edge loads before the arrive
+    if (lane == 0) {
+        StageHeader* h = reinterpret_cast<StageHeader*>(st);
+        h->c0 = c0; h->nA = nA; h->nB = nB;
+        h->mA1 = mA1; h->mA0 = mA0; h->mB1 = mB1; h->mB0 = mB0;
+        h->kA = oKA; h->vA = oVA; h->kB = oKB; h->vB = oVB;
+        h->end = 0;
+        mbar_arrive_expect_tx(&full[s], tx);
+    }
+    __syncwarp();
+    uint32_t unused = 0;
+    if (lane < 4) stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], unused, 1);
+    ++k;
+    return true;
+}
+
+// End marker for the consumers after the last fill (lane 0).
+template <int S_IN>
+__device__ __forceinline__ void stage_end(const EngineArgs& g, uint8_t* smem, uint64_t* full, uint64_t* empty,
+                                          int lane, int k) {
+    if (lane != 0) return;
+    const int s = k % S_IN;
+    if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns)) {
+        set_status(g.status, TM_ERR_TIMEOUT);
+    } else {
+        StageHeader* h = reinterpret_cast<StageHeader*>(smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes);
+        h->end = 1;
+        mbar_arrive_expect_tx(&full[s], 0);
+    }
+}
+
 // Producer warp: pulls tile records from the work queue and stages them.
 // A grab of G consecutive records is packed greedily into tiles of at most
 // `cap` elements (consecutive records are adjacent on the merge path).
-// Lanes 0..3 handle the four pieces (A keys, A payloads, B keys, B payloads)
-// in parallel; lane 0 writes the header and arms the stage's barrier.
-template <typename K, int LOG_T, int S_IN, int SPLIT, bool FUSED>
+template <typename K, typename V, int LOG_T, int S_IN, int SPLIT>
 __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                 uint64_t* empty, int lane) {
     int k = 0;                                        // fills issued
@@ -441,13 +511,13 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
     if (lane == 0) base = atomicAdd(g.queue, (unsigned long long)G);
     base = __shfl_sync(0xffffffffu, base, 0);
     TileDesc d{};
-    if (lane < G && base + lane < nitems) d = engine_record<FUSED>(g, (int64_t)(base + lane));
+    if (lane < G && base + lane < nitems) d = g.desc[base + lane];
     while (ok && base < nitems) {
         unsigned long long nbase = 0;                 // prefetch the next grab
         if (lane == 0) nbase = atomicAdd(g.queue, (unsigned long long)G);
         nbase = __shfl_sync(0xffffffffu, nbase, 0);
         TileDesc nd{};
-        if (lane < G && nbase + lane < nitems) nd = engine_record<FUSED>(g, (int64_t)(nbase + lane));
+        if (lane < G && nbase + lane < nitems) nd = g.desc[nbase + lane];
         const int avail = (int)min((unsigned long long)G, nitems - base);
         for (int q = 0; q < avail && ok;) {
             const int64_t a0 = __shfl_sync(0xffffffffu, d.a0, q);
@@ -464,85 +534,154 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
                 nA += xA;
                 nB += xB;
             }
-            if (nA + nB == 0) continue;
-            if (nA < 0 || nB < 0 || nA + nB > g.cap) {
-                if (lane == 0) set_status(g.status, TM_ERR_BOUNDS);
-                continue;
-            }
-            const int s = k % S_IN;
-            int free_ok = 1;
-            if (lane == 0 && k >= S_IN)
-                free_ok = mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns) ? 1 : 0;
-            free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
-            if (!free_ok) {
-                if (lane == 0) set_status(g.status, TM_ERR_TIMEOUT);
-                ok = false;
-                break;
-            }
-            if (k == g.drop_fill) {                    // testing: this stage never becomes ready
-                ++k;
-                continue;
-            }
-            uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
-            // piece of this lane: 0 A keys, 1 A payloads, 2 B keys, 3 B payloads
-            const bool isB = lane >= 2, isV = (lane & 1) != 0;
-            const uint32_t E = isV ? 4u : (uint32_t)sizeof(K);
-            const void* pbase = isB ? (isV ? (const void*)g.Bv : g.B) : (isV ? (const void*)g.Av : g.A);
-            // keys-only merge (no payload arrays): the payload pieces are empty
-            const int64_t plen = isB ? g.lenB : g.lenA, plo = isB ? b0 : a0;
-            const int64_t pcnt = (isV && g.Cv == nullptr) ? 0 : (isB ? nB : nA);
-            uint8_t* region = st + (isV ? g.lay.vals_off : g.lay.keys_off);
-            uint32_t dst_off = 0;
-            if (isB) {   // after the A piece of the same region, on a 16-byte boundary
-                const uintptr_t abase = reinterpret_cast<uintptr_t>(isV ? (const void*)g.Av : g.A);
-                const uint32_t aoff = (uint32_t)((abase + (uintptr_t)a0 * E) & 15);
-                dst_off = (aoff + (uint32_t)nA * E + 31u) & ~15u;
-            }
-            uint32_t tx = 0, off = 0, inv = 0;
-            if (lane < 4) {
-                off = stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], tx, 0);
-                if (SPLIT == kSplitBlocks) {          // inverses of q+1 and q per piece length
-                    const uint32_t qn = (uint32_t)(isB ? nB : nA) >> LOG_T;
-                    inv = inv31(isV ? qn : qn + 1);
-                }
-            }
-            tx += __shfl_xor_sync(0xffffffffu, tx, 1);
-            tx += __shfl_xor_sync(0xffffffffu, tx, 2);
-            const uint32_t oKA = __shfl_sync(0xffffffffu, off, 0), oVA = __shfl_sync(0xffffffffu, off, 1);
-            const uint32_t oKB = __shfl_sync(0xffffffffu, off, 2), oVB = __shfl_sync(0xffffffffu, off, 3);
-            const uint32_t mA1 = __shfl_sync(0xffffffffu, inv, 0), mA0 = __shfl_sync(0xffffffffu, inv, 1);
-            const uint32_t mB1 = __shfl_sync(0xffffffffu, inv, 2), mB0 = __shfl_sync(0xffffffffu, inv, 3);
-            __syncwarp();                              // plain edge loads before the arrive
-            if (lane == 0) {
-                StageHeader* h = reinterpret_cast<StageHeader*>(st);
-                h->c0 = c0; h->nA = nA; h->nB = nB;
-                h->mA1 = mA1; h->mA0 = mA0; h->mB1 = mB1; h->mB0 = mB0;
-                h->kA = oKA; h->vA = oVA; h->kB = oKB; h->vB = oVB;
-                h->end = 0;
-                mbar_arrive_expect_tx(&full[s], tx);
-            }
-            __syncwarp();
-            uint32_t unused = 0;
-            if (lane < 4) stage_piece(region, dst_off, pbase, plen, plo, pcnt, E, &full[s], unused, 1);
-            ++k;
+            ok = stage_tile<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, lane, k, a0, b0, c0, nA, nB);
         }
         base = nbase;
         d = nd;
     }
-    if (lane == 0 && ok) {                            // end marker for the consumers
-        const int s = k % S_IN;
-        if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns)) {
-            set_status(g.status, TM_ERR_TIMEOUT);
-        } else {
-            StageHeader* h = reinterpret_cast<StageHeader*>(smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes);
-            h->end = 1;
-            mbar_arrive_expect_tx(&full[s], 0);
+    if (ok) stage_end<S_IN>(g, smem, full, empty, lane, k);
+}
+
+// Fused single merge, Steps 3-4 selection done by each CTA for itself: the
+// subproblems of A-side PEs ca + lane and B-side PEs cb + lane (lanes whose
+// PE is below `end` and whose block is not empty), with their indices on the
+// merge-path chain, from the cross ranks this launch wrote (read through L2).
+// The cross ranks of a PE and of the next one are loaded together in one
+// round; the one further rank the split-point form may need (ybar of the
+// first B block at or after xbar_i, xbar of the first A block at or after
+// ybar_j) usually lies in the other side's window, so it comes from a lane
+// of the warp, and from L2 only when it does not.  Lanes without a record
+// get chain = INT64_MAX.
+struct FusedRec { int64_t a0, b0, chain; int32_t nA, nB; };
+
+__device__ __forceinline__ void fused_records(const EngineArgs& g, int64_t ca, int64_t cb, int64_t end, int lane,
+                                              FusedRec& ra, FusedRec& rb) {
+    const int64_t n = g.lenA, m = g.lenB, p = g.fp;
+    const long long* fx = reinterpret_cast<const long long*>(g.fx);
+    const long long* fy = reinterpret_cast<const long long*>(g.fy);
+    const int64_t i = ca + lane, j = cb + lane;
+    const Blocks32& bA = g.fbA;
+    const Blocks32& bB = g.fbB;
+    const bool va = i < end && bA.start(i) < n;
+    const bool vb = j < end && bB.start(j) < m;
+    // one round: xbar_i, xbar_{i+1}, ybar_j, ybar_{j+1} (indices <= p)
+    const int64_t xa = va ? (int64_t)__ldcg(fx + i) : 0, xa1 = va ? (int64_t)__ldcg(fx + i + 1) : 0;
+    const int64_t ya = vb ? (int64_t)__ldcg(fy + j) : 0, ya1 = vb ? (int64_t)__ldcg(fy + j + 1) : 0;
+    // the further rank of each side, from the other side's window when it is there
+    const int64_t jn = va ? bB.first_at_or_after(xa) : cb;
+    const int64_t in = vb ? bA.first_at_or_after(ya) : ca;
+    const int64_t dj = jn - cb, di = in - ca;
+    const int64_t yw = __shfl_sync(0xffffffffu, ya, (int)(dj >= 0 && dj < 32 ? dj : 0));
+    const int64_t yw1 = __shfl_sync(0xffffffffu, ya1, 31);
+    const int64_t xw = __shfl_sync(0xffffffffu, xa, (int)(di >= 0 && di < 32 ? di : 0));
+    const int64_t xw1 = __shfl_sync(0xffffffffu, xa1, 31);
+    // the window holds ybar[cb .. cb + 32] of valid lanes only: lane 31's
+    // ybar_{j+1} counts when lane 31 is valid, any lane's ybar_j when it is
+    const bool yin = dj >= 0 && dj < 32 && cb + dj < end && bB.start(cb + dj) < m;
+    const bool yin1 = dj == 32 && cb + 31 < end && bB.start(cb + 31) < m;
+    const bool xin = di >= 0 && di < 32 && ca + di < end && bA.start(ca + di) < n;
+    const bool xin1 = di == 32 && ca + 31 < end && bA.start(ca + 31) < n;
+    ra = FusedRec{0, 0, INT64_MAX, 0, 0};
+    rb = FusedRec{0, 0, INT64_MAX, 0, 0};
+    if (va) {
+        // subproblem_of asks an A-side PE for xbar(i), xbar(i+1) and ybar(jn) only
+        auto xq = [&](int64_t k) { return k == i ? xa : xa1; };
+        auto yq = [&](int64_t k) {
+            return yin ? yw : (yin1 ? yw1 : (int64_t)__ldcg(fy + k));
+        };
+        int64_t a0, a1, b0, b1;
+        subproblem_in<int64_t>(true, i, p, bA, bB, xq, yq, a0, a1, b0, b1);
+        ra = FusedRec{a0, b0, i + jn, (int32_t)(a1 - a0), (int32_t)(b1 - b0)};
+    }
+    if (vb) {
+        // and a B-side PE for ybar(j), ybar(j+1) and xbar(in) only
+        auto yq = [&](int64_t k) { return k == j ? ya : ya1; };
+        auto xq = [&](int64_t k) {
+            return xin ? xw : (xin1 ? xw1 : (int64_t)__ldcg(fx + k));
+        };
+        int64_t a0, a1, b0, b1;
+        subproblem_in<int64_t>(false, j, p, bA, bB, xq, yq, a0, a1, b0, b1);
+        rb = FusedRec{a0, b0, j + in, (int32_t)(a1 - a0), (int32_t)(b1 - b0)};
+    }
+}
+
+// Producer of the fused single merge.  CTA c owns the processing elements
+// [c p / G, (c+1) p / G) of both sides (G CTAs), computes their subproblems
+// itself (no records are published, so no second grid barrier), takes them
+// in merge-path order and packs chain-adjacent ones (consecutive chain
+// indices: contiguous in A, B and C) into tiles of at most `cap` elements.
+// Lanes hold up to 32 records of each side at a time.
+template <typename K, typename V, int LOG_T, int S_IN, int SPLIT>
+__device__ __forceinline__ void engine_producer_static(const EngineArgs& g, uint8_t* smem, uint64_t* full,
+                                                       uint64_t* empty, int lane) {
+    const int64_t p = g.fp, G = gridDim.x, c = blockIdx.x;
+    const int64_t i0 = c * p / G, i1 = (c + 1) * p / G;
+    int64_t ca = i0, cb = i0;                         // first PE of the batch held in the lanes
+    FusedRec ra, rb;
+    fused_records(g, ca, cb, i1, lane, ra, rb);
+    if (g.trace != nullptr && lane == 0) {            // selection of the first records done
+        const uint64_t t = global_timer_ns();
+        g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 3] = t;
+        g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 4] = t;
+    }
+    int qa = 0, qb = 0, k = 0;
+    bool ok = true;
+    int64_t ta0 = 0, tb0 = 0, tnext = -1;             // the tile being packed
+    int tA = 0, tB = 0;
+    while (ok) {
+        if (qa == 32 || qb == 32) {                   // next window of the exhausted side
+            FusedRec na, nb;
+            if (qa == 32) { ca += 32; qa = 0; }
+            if (qb == 32) { cb += 32; qb = 0; }
+            fused_records(g, ca, cb, i1, lane, na, nb);
+            if (qa == 0) ra = na;
+            if (qb == 0) rb = nb;
         }
+        const int64_t cha = __shfl_sync(0xffffffffu, ra.chain, qa);
+        const int64_t chb = __shfl_sync(0xffffffffu, rb.chain, qb);
+        if (cha == INT64_MAX && chb == INT64_MAX) break;
+        const bool takeA = cha < chb;                 // warp-uniform
+        const FusedRec& r = takeA ? ra : rb;
+        const int q = takeA ? qa : qb;
+        const int64_t chain = takeA ? cha : chb;
+        const int64_t a0 = __shfl_sync(0xffffffffu, r.a0, q);
+        const int64_t b0 = __shfl_sync(0xffffffffu, r.b0, q);
+        const int nA = __shfl_sync(0xffffffffu, r.nA, q);
+        const int nB = __shfl_sync(0xffffffffu, r.nB, q);
+        if (takeA) ++qa; else ++qb;
+        if (chain == tnext && tA + tB + nA + nB <= g.cap) {   // extends the tile along the merge path
+            tA += nA;
+            tB += nB;
+            ++tnext;
+            continue;
+        }
+        ok = stage_tile<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, lane, k, ta0, tb0, ta0 + tb0, tA, tB);
+        ta0 = a0; tb0 = b0; tA = nA; tB = nB; tnext = chain + 1;
+    }
+    if (ok) ok = stage_tile<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, lane, k, ta0, tb0, ta0 + tb0, tA, tB);
+    if (ok) stage_end<S_IN>(g, smem, full, empty, lane, k);
+}
+
+// Prefetch into L2 of this CTA's share (1/parts, 16-byte granules, inside the
+// array's own aligned span) of an array of len elements of E bytes.
+__device__ __forceinline__ void prefetch_share_l2(const void* base, int64_t len, uint32_t E, int64_t part,
+                                                  int64_t parts) {
+    if (base == nullptr || len <= 0) return;
+    const uint64_t b = reinterpret_cast<uint64_t>(base);
+    const uint64_t lo = (b + 15) & ~15ull, hi = (b + (uint64_t)len * E) & ~15ull;
+    if (hi <= lo) return;
+    const uint64_t per = (((hi - lo) + parts - 1) / parts + 15) & ~15ull;
+    const uint64_t s = lo + (uint64_t)part * per;
+    if (s >= hi) return;
+    const uint64_t e = s + per < hi ? s + per : hi;
+    for (uint64_t x = s; x < e; x += (1ull << 30)) {
+        const uint32_t sz = (uint32_t)((e - x) < (1ull << 30) ? (e - x) : (1ull << 30));
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(x), "r"(sz) : "memory");
     }
 }
 
 // Consumers, paper's rule inside the CTA (output via separate buffers).
-template <typename K, int LOG_T, int S_IN, int S_OUT>
+template <typename K, typename V, int LOG_T, int S_IN, int S_OUT>
 __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                         uint64_t* empty, int tid) {
     constexpr int T = 1 << LOG_T;
@@ -563,14 +702,14 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
         const int64_t c0 = h->c0;
         const K* kA = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kA);
         const K* kB = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kB);
-        const uint32_t* vA = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vA);
-        const uint32_t* vB = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vB);
+        const V* vA = reinterpret_cast<const V*>(st + g.lay.vals_off + h->vA);
+        const V* vB = reinterpret_cast<const V*>(st + g.lay.vals_off + h->vB);
         const BlockSplit<LOG_T> SA(nA, h->mA1, h->mA0), SB(nB, h->mB1, h->mB0);
         uint8_t* ob_base = smem + g.lay.outs_off + (uint32_t)ob * g.lay.out_bytes;
         const uintptr_t gk = reinterpret_cast<uintptr_t>(g.C) + (uintptr_t)c0 * sizeof(K);
-        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * 4;
+        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * sizeof(V);
         K* oK = reinterpret_cast<K*>(ob_base + (gk & 15));
-        uint32_t* oV = reinterpret_cast<uint32_t*>(ob_base + g.lay.out_vals_off + (gv & 15));
+        V* oV = reinterpret_cast<V*>(ob_base + g.lay.out_vals_off + (gv & 15));
 
         // Steps 1-2 inside the tile
         {
@@ -609,7 +748,7 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
         if (leader) mbar_arrive_expect_tx(&empty[s], 0);         // input stage s may be refilled
         const int L = nA + nB;
         store_out<K>(ob_base, g.C, c0, L, tid, T, leader);
-        store_out<uint32_t>(ob_base + g.lay.out_vals_off, g.Cv, c0, L, tid, T, leader);
+        store_out<V>(ob_base + g.lay.out_vals_off, g.Cv, c0, L, tid, T, leader);
         if (leader) bulk_commit();
     }
     if (leader) bulk_wait_read<0>();
@@ -618,34 +757,47 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
 // Consumers, equal output runs of VT elements per thread, results written
 // back into the consumed stage.  The stage is released one tile later, once
 // its bulk store has read it.
-template <typename K, int LOG_T, int S_IN, int VT, bool VALS>
+template <typename K, typename V, int LOG_T, int S_IN, int VT, bool VALS>
 __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                           uint64_t* empty, int tid) {
     constexpr int T = 1 << LOG_T;
     const bool leader = (tid == 0);
     int pending = -1;                                  // stage whose store is still reading it
-    for (int k = 0;; ++k) {
+    int k = 0;
+    for (;; ++k) {
         const int s = k % S_IN;
         uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
         if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, g.wait_ns)) {
             if (leader) set_status(g.status, TM_ERR_TIMEOUT);
             break;
         }
+        if (k == 0 && leader && g.trace != nullptr)
+            g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 6] = global_timer_ns();
         const StageHeader* h = reinterpret_cast<const StageHeader*>(st);
         if (h->end) break;
         const int nA = h->nA, nB = h->nB;
         const int64_t c0 = h->c0;
         const K* kA = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kA);
         const K* kB = reinterpret_cast<const K*>(st + g.lay.keys_off + h->kB);
-        const uint32_t* vA = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vA);
-        const uint32_t* vB = reinterpret_cast<const uint32_t*>(st + g.lay.vals_off + h->vB);
+        const V* vA = reinterpret_cast<const V*>(st + g.lay.vals_off + h->vA);
+        const V* vB = reinterpret_cast<const V*>(st + g.lay.vals_off + h->vB);
         const int L = nA + nB;
         const int d0 = tid * VT;
         const int cnt = max(0, min(VT, L - d0));
         constexpr bool vals = VALS;                    // false: keys-only merge
         K rk[VT];
-        uint32_t rv[VT];
-        if (cnt > 0) {
+        V rv[VT];
+        if (cnt > 0 && (nA == 0 || nB == 0)) {         // one side empty (Step 3 case (a), its mirror): a copy
+            const K* ks = nB == 0 ? kA : kB;
+            const V* vs = nB == 0 ? vA : vB;
+#pragma unroll
+            for (int q = 0; q < VT; ++q) {
+                if (q < cnt) {
+                    rk[q] = ks[d0 + q];
+                    if constexpr (vals) rv[q] = vs[d0 + q];
+                }
+            }
+        } else if (cnt > 0) {
             int i = corank_smem(kA, nA, kB, nB, d0);
             int j = d0 - i;
             K ka = kA[i], kb = kB[j];
@@ -655,7 +807,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
                     const bool takeB = (j < nB) && ((i >= nA) || (kb < ka));
                     const int idx = takeB ? j : i;
                     const K* ks = takeB ? kB : kA;
-                    const uint32_t* vs = takeB ? vB : vA;
+                    const V* vs = takeB ? vB : vA;
                     rk[q] = takeB ? kb : ka;
                     if constexpr (vals) rv[q] = vs[idx];
                     const K nxt = ks[idx + 1];
@@ -665,11 +817,11 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         }
         consumer_sync(T);                              // all reads of the stage's input done
         const uintptr_t gk = reinterpret_cast<uintptr_t>(g.C) + (uintptr_t)c0 * sizeof(K);
-        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * 4;
+        const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * sizeof(V);
         uint8_t* bk = st + g.lay.keys_off;
         uint8_t* bv = st + g.lay.vals_off;
         K* oK = reinterpret_cast<K*>(bk + (gk & 15));
-        uint32_t* oV = reinterpret_cast<uint32_t*>(bv + (gv & 15));
+        V* oV = reinterpret_cast<V*>(bv + (gv & 15));
 #pragma unroll
         for (int q = 0; q < VT; ++q) {
             if (q < cnt) {
@@ -680,7 +832,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         fence_proxy_async_smem();
         consumer_sync(T);
         store_out<K>(bk, g.C, c0, L, tid, T, leader);
-        if constexpr (vals) store_out<uint32_t>(bv, g.Cv, c0, L, tid, T, leader);
+        if constexpr (vals) store_out<V>(bv, g.Cv, c0, L, tid, T, leader);
         if (leader) {
             bulk_commit();
             if (pending >= 0) {                         // previous tile's store has read its stage
@@ -691,9 +843,10 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         }
     }
     if (leader) bulk_wait_read<0>();
+    if (leader && g.trace != nullptr) g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 7] = (uint64_t)k;
 }
 
-template <typename K, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT, bool FUSED = false>
+template <typename K, typename V, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT, bool FUSED = false>
 __global__ void __launch_bounds__((1 << LOG_T) + 32)
 merge_engine_kernel(const EngineArgs g) {
     constexpr int T = 1 << LOG_T;
@@ -707,26 +860,35 @@ merge_engine_kernel(const EngineArgs g) {
         fence_proxy_async_smem();
     }
     trace_stamp(g, 0);
+    if constexpr (FUSED) {                            // the inputs of the whole merge into L2, in G shares
+        if (tid == T) {
+            const int64_t c = blockIdx.x, G = gridDim.x;
+            const uint32_t vb = g.Cv ? (uint32_t)sizeof(V) : 0u;
+            prefetch_share_l2(g.A, g.lenA, sizeof(K), c, G);
+            prefetch_share_l2(g.B, g.lenB, sizeof(K), c, G);
+            if (vb) {
+                prefetch_share_l2(g.Av, g.lenA, vb, c, G);
+                prefetch_share_l2(g.Bv, g.lenB, vb, c, G);
+            }
+        }
+    }
     __syncthreads();
-    if constexpr (FUSED) {                            // Steps 1-2, the single synchronisation, the plan
+    if constexpr (FUSED) {                            // Steps 1-2 and the single synchronisation
         fused_cross_ranks<K>(g);
         trace_stamp(g, 1);
         if (!grid_barrier(g.gbar, 1, g.wait_ns, g.status)) return;
         trace_stamp(g, 2);
-        fused_plan(g);
-        trace_stamp(g, 3);
-        if (!grid_barrier(g.gbar, 2, g.wait_ns, g.status)) return;
-        trace_stamp(g, 4);
     }
-    if (tid >= T) {
-        engine_producer<K, LOG_T, S_IN, SPLIT, FUSED>(g, smem, full, empty, tid - T);
+    if (tid >= T) {                                   // Steps 3-4: selection by the producer, then merges
+        if constexpr (FUSED) engine_producer_static<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
+        else                 engine_producer<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
         return;
     }
     if constexpr (SPLIT == kSplitDiagonal) {           // payloads or keys only: one branch per launch
-        if (g.Cv != nullptr) engine_consumers_diagonal<K, LOG_T, S_IN, VT, true>(g, smem, full, empty, tid);
-        else                 engine_consumers_diagonal<K, LOG_T, S_IN, VT, false>(g, smem, full, empty, tid);
+        if (g.Cv != nullptr) engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, true>(g, smem, full, empty, tid);
+        else                 engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, false>(g, smem, full, empty, tid);
     }
-    else engine_consumers_blocks<K, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
+    else engine_consumers_blocks<K, V, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
     trace_stamp(g, 5);
 }
 

@@ -1,7 +1,10 @@
-// Persistent tile-engine kernels for uint64_t keys.
+// Persistent tile-engine kernels for uint64_t keys with 4-byte payloads (and
+// keys-only merges).
 #include "tm_engine_launch.cuh"
 
 namespace pmerge {
+extern template tm_status launch_engine_v64<uint64_t>(const EngineArgs&, const tm_config*, cudaStream_t);
+extern template tm_status launch_engine_fused_v64<uint64_t>(const EngineArgs&, cudaStream_t);
 template tm_status launch_engine<uint64_t>(const EngineArgs&, const tm_config*, cudaStream_t);
 template tm_status launch_engine_fused<uint64_t>(const EngineArgs&, cudaStream_t);
 }  // namespace pmerge

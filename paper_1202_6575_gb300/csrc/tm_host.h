@@ -38,9 +38,9 @@ inline tm_status cuda_failed(cudaError_t e) {
 // arrays (each 4-byte aligned when its side is not empty), or, for a
 // keys-only merge, none (the output payload pointer NULL, and so the input
 // ones).
-inline bool payloads_ok(int64_t n, const void* a, int64_t m, const void* b, const void* c) {
+inline bool payloads_ok(int64_t n, const void* a, int64_t m, const void* b, const void* c, int vsize = 4) {
     if (c == nullptr) return a == nullptr && b == nullptr;
-    return (n == 0 || aligned(a, 4)) && (m == 0 || aligned(b, 4)) && aligned(c, 4);
+    return (n == 0 || aligned(a, vsize)) && (m == 0 || aligned(b, vsize)) && aligned(c, vsize);
 }
 
 // Bytes of one payload word selected by cfg (tm_config.payload_bytes: 0 or 4

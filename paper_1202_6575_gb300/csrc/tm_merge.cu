@@ -308,6 +308,7 @@ static tm_status merge_tiles_typed(const void* a_keys, const uint32_t* a_vals, i
     a.A = a_keys; a.Av = a_vals; a.lenA = n;
     a.B = b_keys; a.Bv = b_vals; a.lenB = m;
     a.C = c_keys; a.Cv = c_vals;
+    a.vbytes = payload_size(cfg);
     a.cap = cap;
     return launch_engine<K>(a, cfg, s);
 }
@@ -433,8 +434,11 @@ static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t*
         a.A = a_keys; a.Av = a_vals; a.lenA = n;
         a.B = b_keys; a.Bv = b_vals; a.lenB = m;
         a.C = c_keys; a.Cv = c_vals;
+        a.vbytes = payload_size(cfg);
         a.cap = (int)cap;
         a.fx = w.xbar; a.fy = w.ybar; a.fp = p;
+        a.fbA = Blocks32((uint32_t)n, (uint32_t)p);     // n, m <= kFusedMaxBlocks * kFusedMaxCap < 2^31
+        a.fbB = Blocks32((uint32_t)m, (uint32_t)p);
         a.gbar = reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(w.control) + 16);
         a.trace = w.trace;
         const tm_status st = launch_engine_fused<K>(a, s);
@@ -526,10 +530,10 @@ tm_status tm_merge(tm_key_type kt,
                    void* workspace, size_t workspace_bytes,
                    const tm_config* cfg, tm_stream_t stream) {
     if (n < 0 || m < 0) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) < 0) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
-        !payloads_ok(n, a_vals, m, b_vals, c_vals))
+        !payloads_ok(n, a_vals, m, b_vals, c_vals, payload_size(cfg)))
         return TM_ERR_INVALID;
     const int64_t p = choose_blocks(n, m, cfg);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p, cfg))
@@ -592,10 +596,10 @@ tm_status tm_merge_tiles(tm_key_type kt,
                          void* c_keys, uint32_t* c_vals, void* control,
                          const tm_config* cfg, tm_stream_t stream) {
     if (n < 0 || m < 0 || n_tiles < 0 || cap < 1 || !aligned(control, 256)) return TM_ERR_INVALID;
-    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) != 4) return TM_ERR_UNSUPPORTED;
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || payload_size(cfg) < 0) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
-        !payloads_ok(n, a_vals, m, b_vals, c_vals) || (n_tiles > 0 && !aligned(tiles, 16)))
+        !payloads_ok(n, a_vals, m, b_vals, c_vals, payload_size(cfg)) || (n_tiles > 0 && !aligned(tiles, 16)))
         return TM_ERR_INVALID;
     if (n_tiles == 0 || n + m == 0) return TM_OK;
     return merge_tiles_dispatch(kt, a_keys, a_vals, n, b_keys, b_vals, m, tiles, n_tiles, cap,

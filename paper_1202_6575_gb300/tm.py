@@ -142,6 +142,17 @@ def _check(code: int, where: str):
         raise TmError(code, where + (f" [{tm_last_cuda_error()}]" if code == TM_ERR_CUDA else ""))
 
 
+def _cfg_struct(cfg) -> TmConfig:
+    """A TmConfig holding cfg (None: all defaults)."""
+    c = TmConfig()
+    if isinstance(cfg, TmConfig):
+        ctypes.memmove(ctypes.addressof(c), ctypes.addressof(cfg), ctypes.sizeof(TmConfig))
+    elif cfg:
+        for k, v in dict(cfg).items():
+            setattr(c, k, int(v))
+    return c
+
+
 def _cfg(cfg):
     if cfg is None:
         return None
@@ -169,6 +180,35 @@ def _dev(t, name: str, dtypes=None) -> int:
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     return t.data_ptr() if t.numel() else 0
+
+
+PAYLOAD64_DTYPES = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+ANY_PAYLOAD_DTYPES = PAYLOAD_DTYPES + PAYLOAD64_DTYPES
+
+
+def _payload_cfg(cfg, *vals):
+    """cfg with payload_bytes set from the payload tensors' word size (8 for
+    64-bit payload dtypes, else 4 as given); the tensors must agree."""
+    widths = {8 if v.dtype in PAYLOAD64_DTYPES else 4 for v in vals if v is not None}
+    if len(widths) > 1:
+        raise ValueError("payload tensors mix 32-bit and 64-bit words")
+    width = max(widths) if widths else 4
+    if isinstance(cfg, TmConfig):
+        given = cfg.payload_bytes                  # 0: follow the tensors
+        if widths and given and given != width:
+            raise ValueError(f"cfg.payload_bytes = {given} but the payloads are {width}-byte words")
+        if width == 8 and given != 8:
+            c = TmConfig.from_buffer_copy(cfg)
+            c.payload_bytes = 8
+            return c
+        return cfg
+    d = dict(cfg or {})
+    given = d.get("payload_bytes", 0)
+    if any(v is not None for v in vals) and given and given != width:
+        raise ValueError(f"payload_bytes = {given} but the payloads are {width}-byte words")
+    if width == 8:
+        d["payload_bytes"] = 8
+    return d or cfg
 
 
 def _kt(kt: str) -> int:
@@ -204,15 +244,16 @@ def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, s
         C = torch.empty(n + m, dtype=A.dtype, device=A.device)
     keys_only = Av is None and Bv is None
     if Cv is None and not keys_only:
-        Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
+        Cv = torch.empty(n + m, dtype=(Av if Av is not None else Bv).dtype, device=A.device)
     if C.numel() != n + m or (not keys_only and (Cv.numel() != n + m or Av.numel() != n or Bv.numel() != m)):
         raise ValueError("length mismatch")
+    cfg = _payload_cfg(cfg, Av, Bv, Cv)
     cfgp = _cfg(cfg)
     if workspace is None:
         workspace = new_workspace(tm_merge_workspace_size(n, m, cfg), A.device)
-    code = load().tm_merge(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), n, _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), m,
-                           _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES), _dev(workspace, "workspace"),
-                           workspace.numel(), cfgp, _stream(stream))
+    code = load().tm_merge(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", ANY_PAYLOAD_DTYPES), n, _dev(B, "B", kd),
+                           _dev(Bv, "Bv", ANY_PAYLOAD_DTYPES), m, _dev(C, "C", kd), _dev(Cv, "Cv", ANY_PAYLOAD_DTYPES),
+                           _dev(workspace, "workspace"), workspace.numel(), cfgp, _stream(stream))
     _check(code, "tm_merge")
     return C, Cv, workspace
 
@@ -263,11 +304,13 @@ def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None,
     if C is None:
         C = torch.empty(n + m, dtype=A.dtype, device=A.device)
     if Cv is None and (Av is not None or Bv is not None):
-        Cv = torch.empty(n + m, dtype=torch.int32, device=A.device)
+        Cv = torch.empty(n + m, dtype=(Av if Av is not None else Bv).dtype, device=A.device)
     if control is None:
         control = torch.zeros(256, dtype=torch.uint8, device=A.device)
-    code = load().tm_merge_tiles(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), n, _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), m,
-                                 _dev(tiles, "tiles"), n_tiles, cap, _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES),
+    cfg = _payload_cfg(cfg, Av, Bv, Cv)
+    P = ANY_PAYLOAD_DTYPES
+    code = load().tm_merge_tiles(_kt(kt), _dev(A, "A", kd), _dev(Av, "Av", P), n, _dev(B, "B", kd), _dev(Bv, "Bv", P),
+                                 m, _dev(tiles, "tiles"), n_tiles, cap, _dev(C, "C", kd), _dev(Cv, "Cv", P),
                                  _dev(control, "control"), _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_tiles")
     return C, Cv, control
@@ -351,10 +394,11 @@ def _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv):
     if C is None:
         C = torch.empty(ta + tb, dtype=A.dtype, device=A.device)
     if Cv is None and (Av is not None or Bv is not None):
-        Cv = torch.empty(ta + tb, dtype=torch.int32, device=A.device)
-    args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av", PAYLOAD_DTYPES), ta,
-            _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv", PAYLOAD_DTYPES), tb,
-            _dev(C, "C", kd), _dev(Cv, "Cv", PAYLOAD_DTYPES))
+        Cv = torch.empty(ta + tb, dtype=(Av if Av is not None else Bv).dtype, device=A.device)
+    P = ANY_PAYLOAD_DTYPES
+    args = (_kt(kt), pairs, _dev(a_off, "a_off", (torch.int64,)), _dev(A, "A", kd), _dev(Av, "Av", P), ta,
+            _dev(b_off, "b_off", (torch.int64,)), _dev(B, "B", kd), _dev(Bv, "Bv", P), tb,
+            _dev(C, "C", kd), _dev(Cv, "Cv", P))
     return args, C, Cv, pairs, ta, tb
 
 
@@ -362,6 +406,7 @@ def tm_merge_batched(kt: str, a_off, A, Av, b_off, B, Bv, C=None, Cv=None, works
                      stream=None):
     """Independent stable merges of CSR pairs; returns (C, Cv, workspace)."""
     args, C, Cv, pairs, ta, tb = _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv)
+    cfg = _payload_cfg(cfg, Av, Bv, Cv)
     if workspace is None:
         workspace = new_workspace(tm_merge_batched_workspace_size(pairs, ta, tb, cfg), A.device)
     code = load().tm_merge_batched(*args, _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg),
@@ -382,10 +427,11 @@ def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=N
         tmp_keys = torch.empty_like(keys)
     if tmp_vals is None and vals is not None:    # vals None: keys-only sort
         tmp_vals = torch.empty_like(vals)
+    cfg = _payload_cfg(cfg, vals, tmp_vals)
     if workspace is None:
         workspace = new_workspace(tm_merge_sort_workspace_size(n, cfg), keys.device)
-    code = load().tm_merge_sort(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals", PAYLOAD_DTYPES), n,
-                                _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", PAYLOAD_DTYPES),
+    code = load().tm_merge_sort(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals", ANY_PAYLOAD_DTYPES), n,
+                                _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", ANY_PAYLOAD_DTYPES),
                                 _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_sort")
     return keys, vals, workspace
@@ -393,7 +439,7 @@ def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=N
 
 def tm_autotune_batched(kt: str, a_off, A, Av, b_off, B, Bv, C, Cv, workspace, stream=None) -> dict:
     args, C, Cv, pairs, ta, tb = _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv)
-    best = TmConfig()
+    best = _cfg_struct(_payload_cfg(None, Av, Bv, Cv))
     code = load().tm_autotune_batched(*args, _dev(workspace, "workspace"), workspace.numel(),
                                       ctypes.byref(best), _stream(stream))
     _check(code, "tm_autotune_batched")
@@ -402,10 +448,11 @@ def tm_autotune_batched(kt: str, a_off, A, Av, b_off, B, Bv, C, Cv, workspace, s
 
 def tm_autotune_sort(kt: str, src_keys, src_vals, keys, vals, tmp_keys, tmp_vals, workspace, stream=None) -> dict:
     kd = TORCH_KEY_DTYPES[kt]
-    best = TmConfig()
-    code = load().tm_autotune_sort(_kt(kt), _dev(src_keys, "src_keys", kd), _dev(src_vals, "src_vals", PAYLOAD_DTYPES),
-                                   src_keys.numel(), _dev(keys, "keys", kd), _dev(vals, "vals", PAYLOAD_DTYPES),
-                                   _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", PAYLOAD_DTYPES),
+    best = _cfg_struct(_payload_cfg(None, src_vals, vals, tmp_vals))
+    P = ANY_PAYLOAD_DTYPES
+    code = load().tm_autotune_sort(_kt(kt), _dev(src_keys, "src_keys", kd), _dev(src_vals, "src_vals", P),
+                                   src_keys.numel(), _dev(keys, "keys", kd), _dev(vals, "vals", P),
+                                   _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", P),
                                    _dev(workspace, "workspace"), workspace.numel(), ctypes.byref(best),
                                    _stream(stream))
     _check(code, "tm_autotune_sort")

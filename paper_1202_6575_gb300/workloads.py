@@ -43,6 +43,16 @@ def payload(src: int, count: int, device, start: int = 0) -> torch.Tensor:
     return word.to(torch.int32)
 
 
+def widen_payload(word32: torch.Tensor) -> torch.Tensor:
+    """64-bit payload words (int64 tensor) from 32-bit ones: the 32-bit word
+    in the high half and a multiplicative hash of it (by 0x9E3779B1, mod
+    2**32) in the low half, so that every bit of the wider word carries
+    information and each 64-bit word names its 32-bit source uniquely."""
+    t = word32.to(torch.int64) & 0xFFFFFFFF
+    low = (t * 0x9E3779B1) & 0xFFFFFFFF                # wraps mod 2**64; the low 32 bits are exact
+    return (t << 32) | low
+
+
 def sorted_uniform_int(count: int, lo: int, hi: int, dtype, g, device) -> torch.Tensor:
     """Sorted sample of `count` i.i.d. integers uniform in [lo, hi)."""
     if count == 0:

@@ -14,4 +14,8 @@ int64_t h_block_of64(int64_t len, int64_t p, int64_t k) { return pmerge::block_o
 int64_t h_first_block64(int64_t len, int64_t p, int64_t k) {
     return pmerge::first_block_at_or_after<int64_t>(len, p, k);
 }
+uint32_t h_fastdiv32(uint32_t x, uint32_t d) { return pmerge::FastDiv32(d).div(x); }
+int64_t h_blocks32_start(uint32_t len, uint32_t p, int64_t i) { return pmerge::Blocks32(len, p).start(i); }
+int64_t h_blocks32_of(uint32_t len, uint32_t p, int64_t k) { return pmerge::Blocks32(len, p).of(k); }
+int64_t h_blocks32_first(uint32_t len, uint32_t p, int64_t k) { return pmerge::Blocks32(len, p).first_at_or_after(k); }
 }

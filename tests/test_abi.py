@@ -163,11 +163,20 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
     ct = tm.TmConfig(trace=1)
     assert lib.tm_merge_phase_times(P(256), 10, 10, ctypes.byref(ct), None, None) == INV
     assert lib.tm_merge_phase_times(P(8), 10, 10, ctypes.byref(ct), ctypes.cast(out6, ctypes.c_void_p), None) == INV
-    # 8-byte payload words are not taken by these calls yet
+    # payload words: 4 or 8 bytes; 8-byte words need 8-byte alignment; the
+    # learned and allocation-free calls take 4-byte words only
     c8 = tm.TmConfig(payload_bytes=8)
-    assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(c8), None) == UNS
-    c3 = tm.TmConfig(payload_bytes=3)
-    assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(c3), None) == UNS
+    v4only, v8 = P(260), P(264)                                # 4-byte but not 8-byte aligned; 8-byte aligned
+    assert lib.tm_merge(0, k8, v4only, 10, k8, v8, 10, k8, v8, P(256), 1 << 20, ctypes.byref(c8), None) == INV
+    assert lib.tm_merge(0, k8, v8, 10, k8, v8, 10, k8, v4only, P(256), 1 << 20, ctypes.byref(c8), None) == INV
+    assert lib.tm_merge_batched(0, 1, P(16), k8, v4only, 10, P(16), k8, v8, 10, k8, v8, P(256), 1 << 30,
+                                ctypes.byref(c8), None) == INV
+    assert lib.tm_merge_sort(0, k8, v4only, 10, k8, v8, P(256), 1 << 30, ctypes.byref(c8), None) == INV
+    assert lib.tm_merge_noalloc(0, k8, v8, 10, k8, v8, 10, k8, v8, None, ctypes.byref(c8), None) == UNS
+    for bad in (3, 2, 16, -4):
+        cb = tm.TmConfig(payload_bytes=bad)
+        assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(cb), None) == UNS
+        assert lib.tm_merge_sort(0, k8, v4, 10, k8, v4, P(256), 1 << 30, ctypes.byref(cb), None) == UNS
     # configurations tm_merge refuses are refused here too (before any device work)
     for bad in ({"partition": tm.TM_PARTITION_DIAGONALS}, {"partition": 7}, {"threads": 64}, {"threads": 384}):
         c = tm.TmConfig(**bad)
@@ -247,3 +256,19 @@ def test_binding_struct_matches_the_c_layout(tmp_path):
                  for name, _ in tm.TmConfig._fields_]
     assert [(n, int(o), int(s)) for n, o, s in c_fields] == py_fields
     assert c_size == ctypes.sizeof(tm.TmConfig)
+
+
+def test_binding_derives_the_payload_width_from_the_tensors():
+    import torch
+    v32, v64 = torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.int64)
+    assert tm._payload_cfg(None, v32, v32) is None
+    assert tm._payload_cfg(None, v64, v64) == {"payload_bytes": 8}
+    assert tm._payload_cfg({"p": 4}, v64, None) == {"p": 4, "payload_bytes": 8}
+    assert tm._payload_cfg({"payload_bytes": 8}, v64) == {"payload_bytes": 8}
+    assert tm._payload_cfg(tm.TmConfig(p=3), v64).payload_bytes == 8
+    with pytest.raises(ValueError):
+        tm._payload_cfg(None, v32, v64)
+    with pytest.raises(ValueError):
+        tm._payload_cfg({"payload_bytes": 4}, v64)
+    with pytest.raises(ValueError):
+        tm._payload_cfg(tm.TmConfig(payload_bytes=8), v32)

@@ -48,6 +48,13 @@ def lib(tmp_path_factory):
         f = getattr(L, name)
         f.restype = i32
         f.argtypes = [i32] * (2 if "div" in name else 3)
+    u32 = ctypes.c_uint32
+    L.h_fastdiv32.restype = u32
+    L.h_fastdiv32.argtypes = [u32, u32]
+    for name in ("h_blocks32_start", "h_blocks32_of", "h_blocks32_first"):
+        f = getattr(L, name)
+        f.restype = i64
+        f.argtypes = [u32, u32, i64]
     return L
 
 
@@ -112,3 +119,47 @@ def test_division_fast_path_boundaries(lib):
     for a in (0, 1, 5, (1 << 31) - 1):
         for b in (1, 2, 3, (1 << 31) - 1):
             assert lib.h_div_nonneg32(a, b) == a // b
+
+
+def test_invariant_divisor_division_against_exact_integers(lib):
+    """FastDiv32 (division by an invariant divisor through a 64-bit
+    reciprocal, Lemire, Kaser and Kurz 2019) equals floor(x / d) for 32-bit
+    x and d: every divisor up to 300 against every x up to 2000, and random
+    and boundary pairs over the whole range."""
+    for d in range(1, 301):
+        for x in list(range(0, 2001)) + [(1 << 32) - 1, (1 << 32) - d, (1 << 31) + 7]:
+            assert lib.h_fastdiv32(x, d) == x // d, (x, d)
+    rng = np.random.default_rng(5)
+    edge = [1, 2, 3, 5, 7, 641, 65535, 65536, 65537, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, (1 << 32) - 1]
+    xs = [int(v) for v in rng.integers(0, 1 << 32, 4000)] + [0, 1, (1 << 32) - 1, (1 << 31), (1 << 31) - 1]
+    ds = [int(v) for v in rng.integers(1, 1 << 32, 400)] + edge + [1 << k for k in range(32)]
+    for d in ds:
+        for x in xs[:200] + [d - 1, d, d + 1, 2 * d - 1, 2 * d] if d < (1 << 31) else xs[:200]:
+            if x < (1 << 32):
+                assert lib.h_fastdiv32(x, d) == x // d, (x, d)
+    for x in xs:
+        d = int(rng.choice(ds))
+        assert lib.h_fastdiv32(x, d) == x // d, (x, d)
+
+
+def test_blocks32_equals_the_general_block_arithmetic(lib):
+    """The fused launch's precomputed 32-bit block decomposition (Blocks32)
+    against the oracle exhaustively on small sizes and against the general
+    64-bit functions on random sizes below 2^31."""
+    for length in range(0, 41):
+        for p in range(1, 14):
+            for i in range(p + 1):
+                assert lib.h_blocks32_start(length, p, i) == oracle.block_start(length, p, i)
+            for k in range(length + 1):
+                assert lib.h_blocks32_of(length, p, k) == oracle.block_of(length, p, k), (length, p, k)
+                assert lib.h_blocks32_first(length, p, k) == first_block_brute(length, p, k), (length, p, k)
+    rng = np.random.default_rng(12)
+    for _ in range(300):
+        length = int(rng.integers(1, 1 << 31))
+        p = int(rng.choice([1, 2, 3, 1024, 16384, int(rng.integers(1, 1 << 20))]))
+        ks = [0, length, length - 1] + [int(v) for v in rng.integers(0, length + 1, 20)]
+        for i in [0, 1, p - 1, p] + [int(v) for v in rng.integers(0, p + 1, 10)]:
+            assert lib.h_blocks32_start(length, p, i) == lib.h_block_start64(length, p, i), (length, p, i)
+        for k in ks:
+            assert lib.h_blocks32_of(length, p, k) == lib.h_block_of64(length, p, k), (length, p, k)
+            assert lib.h_blocks32_first(length, p, k) == lib.h_first_block64(length, p, k), (length, p, k)

@@ -118,3 +118,13 @@ def test_lsm_mixture():
     # 3 standard deviations from the neighbouring means
     lo, mid = np.mean(x < 1.0), np.mean((x >= 1.0) & (x < 3.5))
     assert abs(lo - 1 / 3) < 0.01 and abs(mid - 1 / 3) < 0.01
+
+
+def test_widened_payloads_are_a_bijection_of_the_32_bit_tags():
+    import numpy as np
+    w = torch.tensor([0, 1, -1, 2**31 - 1, -2**31, 12345], dtype=torch.int32)
+    v = W.widen_payload(w).numpy().view(np.uint64)
+    t = w.numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(v >> np.uint64(32), t)
+    assert np.array_equal(v & np.uint64(0xFFFFFFFF), (t * np.uint64(0x9E3779B1)) & np.uint64(0xFFFFFFFF))
+    assert len(set(v.tolist())) == len(v)
