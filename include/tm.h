@@ -120,7 +120,9 @@ typedef struct tm_config {
                            record per-CTA phase timestamps in the workspace (which then needs
                            tm_merge_workspace_size with the same cfg); tm_merge_phase_times
                            reads them */
-    int32_t reserved;
+    int32_t merge_ways; /* tm_merge_sort only: runs merged per pass over memory, 2 (also 0, the
+                           default: one pairwise round per pass) or 4 (two rounds per pass,
+                           below) */
 } tm_config;
 
 /* How tm_merge divides the merge into subproblems.  TM_PARTITION_BLOCKS is
@@ -299,10 +301,17 @@ TM_API size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg);
 /* Stable sort of (keys, vals) by key (Section 3): consecutive runs of 1024
  * elements are sorted inside one CTA each (every element placed by the
  * position formulas of Section 2 over doubling sub-runs), then ceil(log2(n /
- * 1024)) rounds merge adjacent runs pairwise, every round one batched merge
- * of uniform pairs (an unpaired last run is copied).  Rounds alternate
- * between (keys, vals) and (tmp_keys, tmp_vals); the result ends in (keys,
- * vals).  Equal keys keep their input order. */
+ * 1024)) rounds merge adjacent runs pairwise (an unpaired last run is
+ * copied), every round one batched merge of uniform pairs.  With
+ * cfg->merge_ways = 4, two consecutive rounds are done in one pass over
+ * memory: groups of four runs R0..R3 become merge(merge(R0, R1), merge(R2,
+ * R3)), the subproblems chosen by the paper's method on the outer merge of
+ * the two intermediate sequences (which stay in shared memory); a last odd
+ * round is pairwise (pairwise rounds are also taken with cfg->split =
+ * TM_SPLIT_BLOCKS and tiles above 4606).  Passes alternate between (keys,
+ * vals) and (tmp_keys, tmp_vals); the result ends in (keys, vals).  Equal
+ * keys keep their input order.  Other values of merge_ways return
+ * TM_ERR_UNSUPPORTED. */
 TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n,
                                void* tmp_keys, uint32_t* tmp_vals, void* workspace, size_t workspace_bytes,
                                const tm_config* cfg, tm_stream_t stream);

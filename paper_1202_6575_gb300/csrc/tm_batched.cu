@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "tm_engine.cuh"
+#include "tm_engine4.cuh"
 #include "tm_host.h"
 
 namespace pmerge {
@@ -339,6 +340,8 @@ struct BatchedWs {
     int64_t* cta_pair;                             // pair of each search/plan CTA's first thread (CSR)
     int64_t *xbar, *ybar;
     TileDesc* tiles;
+    int4 *ta, *tb;                                 // fused sort rounds: run offsets of every chain point
+    Tile4Desc* tiles4;                             // fused sort rounds: four-run records
     size_t bytes;
 };
 
@@ -350,7 +353,8 @@ static int64_t blocks_bound(int64_t pairs, int64_t total, int64_t tile) { return
 // Workspace: control block, device record count, three per-pair prefix
 // arrays, the scan's CTA totals, the first pair of every search/plan CTA,
 // cross ranks (ranks_cap entries per side) and tile records.
-static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap, int64_t ctas_cap) {
+static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t items_cap, int64_t ctas_cap,
+                           int64_t tuples_cap = 0, int64_t items4_cap = 0) {
     BatchedWs w{};
     uint8_t* b = static_cast<uint8_t*>(base);
     size_t o = 0;
@@ -364,6 +368,9 @@ static BatchedWs ws_layout(void* base, int64_t pairs, int64_t ranks_cap, int64_t
     w.xbar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.ybar = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)ranks_cap * 8, 256);
     w.tiles = reinterpret_cast<TileDesc*>(b + o); o += align_up((size_t)items_cap * sizeof(TileDesc), 256);
+    w.ta = reinterpret_cast<int4*>(b + o); o += align_up((size_t)tuples_cap * sizeof(int4), 256);
+    w.tb = reinterpret_cast<int4*>(b + o); o += align_up((size_t)tuples_cap * sizeof(int4), 256);
+    w.tiles4 = reinterpret_cast<Tile4Desc*>(b + o); o += align_up((size_t)items4_cap * sizeof(Tile4Desc), 256);
     w.bytes = o;
     return w;
 }
@@ -572,17 +579,206 @@ static PairSet sort_round(int64_t n, int64_t run, int64_t tile, int64_t* items) 
     return ps;
 }
 
-// The largest rank and record counts over all merge rounds.
+// ---------------------------------------------------------------------------
+// Two merge-sort rounds fused into one pass: groups of four runs
+// ---------------------------------------------------------------------------
+// Group q holds runs R_k = X[(4q + k) run, (4q + k + 1) run) (clipped to n),
+// k = 0..3.  The pass computes merge(merge(R0, R1), merge(R2, R3)), i.e. the
+// outputs of round `run` and of round 2 run, by the paper's method on the
+// outer merge of X = merge(R0, R1) and Y = merge(R2, R3): p blocks of each,
+// cross ranks of the block starts, the five cases.  X and Y are not stored:
+//  * the x-th element of X and the split of R0, R1 it implies come from the
+//    co-rank of x in (R0, R1) (the position formulas of Section 2); likewise
+//    for Y;
+//  * rank_low(v, Y) = rank_low(v, R2) + rank_low(v, R3), and the first
+//    rank_low(v, Y) elements of Y are exactly R2[0, rank_low(v, R2)) and
+//    R3[0, rank_low(v, R3)); the same holds for rank_high and X.
+// So every chain point P_A(i) = (x_i, xbar_i), P_B(j) = (ybar_j, y_j) of the
+// outer merge comes with the four run offsets (r0, r1, r2, r3) it splits at,
+// and a subproblem between consecutive points is four contiguous ranges.
+
+struct QuadGeom {
+    int64_t start[4], len[4];
+    int64_t base, nX, nY;
+};
+
+__host__ __device__ __forceinline__ QuadGeom quad_geom(int64_t q, int64_t run, int64_t n) {
+    QuadGeom g;
+    g.base = 4 * q * run;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t s0 = g.base + k * run, e = s0 + run < n ? s0 + run : n;
+        g.start[k] = s0 < n ? s0 : n;
+        g.len[k] = e > s0 ? e - s0 : 0;
+    }
+    g.nX = g.len[0] + g.len[1];
+    g.nY = g.len[2] + g.len[3];
+    return g;
+}
+
+// Number of elements of P (nP) among the first d outputs of the stable
+// merge of P and Q (P first on equal keys): the i with Q[d-i-1] < P[i] and
+// P[i-1] <= Q[d-i], by bisection in global memory.
+template <typename K>
+__device__ __forceinline__ int64_t corank_global(const K* __restrict__ P, int64_t nP, const K* __restrict__ Q,
+                                                 int64_t nQ, int64_t d) {
+    int64_t lo = d > nQ ? d - nQ : 0, hi = d < nP ? d : nP;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(Q + (d - mid - 1)) < __ldg(P + mid)) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Chain points of every group: thread (q, local): local < p -> A point i
+// (block start of X), p <= local < 2p -> B point j (block start of Y),
+// local = 2p -> the end points.  xbar / ybar as in Steps 1-2 of the outer
+// merge; ta / tb the run offsets of each point.
+template <typename K>
+__global__ void __launch_bounds__(256)
+quad_search_kernel(const K* __restrict__ X, int64_t n, int64_t run, int64_t p, int64_t groups,
+                   int64_t* __restrict__ xbar, int64_t* __restrict__ ybar, int4* __restrict__ ta,
+                   int4* __restrict__ tb) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t q = div_nonneg<int64_t>(t, 2 * p + 1);
+    if (q >= groups) return;
+    const int64_t local = t - q * (2 * p + 1);
+    const QuadGeom g = quad_geom(q, run, n);
+    const K* R0 = X + g.start[0]; const K* R1 = X + g.start[1];
+    const K* R2 = X + g.start[2]; const K* R3 = X + g.start[3];
+    const int64_t L0 = g.len[0], L1 = g.len[1], L2 = g.len[2], L3 = g.len[3];
+    const int64_t pb = q * (p + 1);
+    const int4 all = make_int4((int)L0, (int)L1, (int)L2, (int)L3);
+    if (local < p) {                                   // A point: block start x of X
+        const int64_t i = local, x = block_start<int64_t>(g.nX, p, i);
+        if (x >= g.nX) { xbar[pb + i] = g.nY; ta[pb + i] = all; return; }
+        const int64_t r0 = corank_global(R0, L0, R1, L1, x), r1 = x - r0;
+        const K v = (r1 < L1 && (r0 >= L0 || __ldg(R1 + r1) < __ldg(R0 + r0))) ? __ldg(R1 + r1) : __ldg(R0 + r0);
+        const int64_t r2 = rank_low_global<K, int64_t>(R2, L2, v), r3 = rank_low_global<K, int64_t>(R3, L3, v);
+        xbar[pb + i] = r2 + r3;
+        ta[pb + i] = make_int4((int)r0, (int)r1, (int)r2, (int)r3);
+    } else if (local < 2 * p) {                        // B point: block start y of Y
+        const int64_t j = local - p, y = block_start<int64_t>(g.nY, p, j);
+        if (y >= g.nY) { ybar[pb + j] = g.nX; tb[pb + j] = all; return; }
+        const int64_t r2 = corank_global(R2, L2, R3, L3, y), r3 = y - r2;
+        const K w = (r3 < L3 && (r2 >= L2 || __ldg(R3 + r3) < __ldg(R2 + r2))) ? __ldg(R3 + r3) : __ldg(R2 + r2);
+        const int64_t r0 = rank_high_global<K, int64_t>(R0, L0, w), r1 = rank_high_global<K, int64_t>(R1, L1, w);
+        ybar[pb + j] = r0 + r1;
+        tb[pb + j] = make_int4((int)r0, (int)r1, (int)r2, (int)r3);
+    } else {                                           // the end points (x_p = nX, y_p = nY)
+        xbar[pb + p] = g.nY; ybar[pb + p] = g.nX;
+        ta[pb + p] = all; tb[pb + p] = all;
+    }
+}
+
+// Records of every group: the subproblem of each non-empty block of X and
+// of Y (the five cases in split-point form, on the outer merge), as the run
+// ranges between its chain point and the next one, at its chain index.
+__global__ void __launch_bounds__(256)
+quad_plan_kernel(int64_t n, int64_t run, int64_t p, int64_t groups, const int64_t* __restrict__ xbar,
+                 const int64_t* __restrict__ ybar, const int4* __restrict__ ta, const int4* __restrict__ tb,
+                 Tile4Desc* __restrict__ desc, int32_t* status) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t q = div_nonneg<int64_t>(t, 2 * p);
+    if (q >= groups) return;
+    const int64_t local = t - q * 2 * p;
+    const QuadGeom g = quad_geom(q, run, n);
+    const bool a_side = local < p;
+    const int64_t pe = a_side ? local : local - p;
+    if (a_side ? block_start<int64_t>(g.nX, p, pe) >= g.nX : block_start<int64_t>(g.nY, p, pe) >= g.nY) return;
+    const int64_t pb = q * (p + 1);
+    auto xb = [&](int64_t i) { return __ldg(xbar + pb + i); };
+    auto yb = [&](int64_t j) { return __ldg(ybar + pb + j); };
+    int64_t a0, a1, b0, b1;
+    subproblem_of<int64_t>(a_side, pe, g.nX, g.nY, p, xb, yb, a0, a1, b0, b1);
+    // the chain point the subproblem ends at: for an A point the next is
+    // P_B(jn) when jn < p and y_jn < xbar_{i+1}, else P_A(i+1) (mirror for B)
+    int4 t0, t1;
+    int64_t chain;
+    if (a_side) {
+        const int64_t jn = first_block_at_or_after<int64_t>(g.nY, p, xb(pe));
+        t0 = ta[pb + pe];
+        t1 = (jn < p && block_start<int64_t>(g.nY, p, jn) < xb(pe + 1)) ? tb[pb + jn] : ta[pb + pe + 1];
+        chain = pe + jn;
+    } else {
+        const int64_t in = first_block_at_or_after<int64_t>(g.nX, p, yb(pe));
+        t0 = tb[pb + pe];
+        t1 = (in < p && block_start<int64_t>(g.nX, p, in) < yb(pe + 1)) ? ta[pb + in] : tb[pb + pe + 1];
+        chain = pe + in;
+    }
+    Tile4Desc d{};
+    // the run offsets must agree with the outer merge's ranges; if not, an
+    // empty record (nothing is read) and TM_ERR_BOUNDS
+    if ((int64_t)t0.x + t0.y != a0 || (int64_t)t0.z + t0.w != b0 || (int64_t)t1.x + t1.y != a1 ||
+        (int64_t)t1.z + t1.w != b1) {
+        set_status(status, TM_ERR_BOUNDS);
+        for (int k = 0; k < 4; ++k) d.s[k] = g.start[k];
+        d.c0 = g.base;
+        d.first = chain == 0;
+        desc[q * 2 * p + chain] = d;
+        return;
+    }
+    d.s[0] = g.start[0] + t0.x; d.s[1] = g.start[1] + t0.y;
+    d.s[2] = g.start[2] + t0.z; d.s[3] = g.start[3] + t0.w;
+    d.l[0] = t1.x - t0.x; d.l[1] = t1.y - t0.y; d.l[2] = t1.z - t0.z; d.l[3] = t1.w - t0.w;
+    d.c0 = g.base + a0 + b0;
+    d.first = chain == 0;
+    desc[q * 2 * p + chain] = d;
+}
+
+template <typename K>
+tm_status launch_engine4(const Engine4Args& a, int vbytes, const tm_config* cfg, cudaStream_t s);
+
+// One fused pair of rounds: runs of `run` sorted in src -> runs of 4 run in dst.
+template <typename K>
+static tm_status run_quads(const BatchedWs& w, int64_t n, int64_t run, int64_t tile, const K* src,
+                           const void* srcv, K* dst, void* dstv, int vbytes, const tm_config* cfg, cudaStream_t s) {
+    const int64_t groups = (n + 4 * run - 1) / (4 * run);
+    const int64_t p = pair_blocks(2 * run, 2 * run, tile);
+    const int64_t threads = groups * (2 * p + 1);
+    if ((threads + 255) / 256 > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    quad_search_kernel<K><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, n, run, p, groups, w.xbar,
+                                                                           w.ybar, w.ta, w.tb);
+    quad_plan_kernel<<<(unsigned)((groups * 2 * p + 255) / 256), 256, 0, s>>>(
+        n, run, p, groups, w.xbar, w.ybar, w.ta, w.tb, w.tiles4, static_cast<int32_t*>(w.control));
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
+    // records: every group but the last has 2p; the last has one per
+    // non-empty block of its X and of its Y
+    const QuadGeom gl = quad_geom(groups - 1, run, n);
+    const int64_t items = (groups - 1) * 2 * p + pair_items(gl.nX, gl.nY, p);
+    Engine4Args a{};
+    a.desc = w.tiles4;
+    a.n_items = items;
+    a.queue = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(w.control) + 8);
+    a.status = static_cast<int32_t*>(w.control);
+    a.src = src; a.srcv = srcv; a.len = n;
+    a.C = dst; a.Cv = dstv;
+    a.cap = (int)(tile + 2);
+    return launch_engine4<K>(a, vbytes, cfg, s);
+}
+
+// Whether the sort fuses pairs of rounds: cfg->merge_ways = 4 asks for it;
+// the four-run engine takes the diagonal in-CTA split only and tiles up to
+// 4606 elements (9-element runs of its 512 consumer threads).
+static bool sort_fuses(const tm_config* cfg, int64_t tile) {
+    if (!cfg || cfg->merge_ways != 4 || cfg->split == TM_SPLIT_BLOCKS) return false;
+    return tile + 2 <= 9 * 512;
+}
+
+// The largest rank, tuple and record counts over all merge rounds.
 static BatchedWs sort_ws_layout(void* base, int64_t n, int64_t tile) {
-    int64_t ranks = 0, items = 0;
+    int64_t ranks = 0, items = 0, tuples = 0, items4 = 0;
     for (int64_t run = kSortRun; run < n; run *= 2) {
         int64_t it = 0;
         PairSet ps = sort_round(n, run, tile, &it);
         const int64_t r = ps.num_pairs * (ps.p_uniform + 1);
         if (r > ranks) ranks = r;
         if (2 * ps.num_pairs * ps.p_uniform > items) items = 2 * ps.num_pairs * ps.p_uniform;
+        const int64_t groups = (n + 4 * run - 1) / (4 * run), p4 = pair_blocks(2 * run, 2 * run, tile);
+        if (groups * (p4 + 1) > tuples) tuples = groups * (p4 + 1);
+        if (groups * 2 * p4 > items4) items4 = groups * 2 * p4;
     }
-    return ws_layout(base, 0, ranks, items, 0);
+    if (tuples > ranks) ranks = tuples;
+    return ws_layout(base, 0, ranks, items, 0, tuples, items4);
 }
 
 template <typename K, typename V>
@@ -594,16 +790,30 @@ static tm_status sort_typed_v(void* keys, void* vals, int64_t n, void* tmp_keys,
     if (n <= 1) return TM_OK;
     K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
     V* bufv[2] = {static_cast<V*>(vals), static_cast<V*>(tmp_vals)};
-    // number of merge rounds decides where the run formation writes, so that
-    // the last round lands in (keys, vals)
+    // pairwise rounds (run 1024, 2048, ...), fused two at a time when the
+    // configuration allows; the number of passes decides where the run
+    // formation writes, so that the last pass lands in (keys, vals)
     int rounds = 0;
     for (int64_t r = kSortRun; r < n; r *= 2) ++rounds;
-    int src = (rounds % 2 == 0) ? 0 : 1;
+    // fused pairs while two rounds remain and the runs' offsets fit int32
+    int fused = 0;
+    if (sort_fuses(cfg, tile))
+        for (int64_t r = kSortRun; rounds - 2 * fused >= 2 && r <= (1LL << 29); r *= 4) ++fused;
+    const int passes = fused + (rounds - 2 * fused);
+    int src = (passes % 2 == 0) ? 0 : 1;
     const int64_t runs = (n + kSortRun - 1) / kSortRun;
     if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
     run_sort_kernel<K, V><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
     if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
-    for (int64_t run = kSortRun; run < n; run *= 2) {
+    int64_t run = kSortRun;
+    for (int f = 0; f < fused; ++f, run *= 4) {
+        const int dst = src ^ 1;
+        tm_status st = run_quads<K>(w, n, run, tile, bufk[src], vals ? bufv[src] : nullptr, bufk[dst],
+                                    vals ? bufv[dst] : nullptr, (int)sizeof(V), cfg, s);
+        if (st != TM_OK) return st;
+        src = dst;
+    }
+    for (; run < n; run *= 2) {
         int64_t items = 0;
         const PairSet ps = sort_round(n, run, tile, &items);
         const int dst = src ^ 1;
@@ -720,6 +930,7 @@ tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, v
     if (n < 0) return TM_ERR_INVALID;
     const int vs = payload_size(cfg);
     if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || vs < 0) return TM_ERR_UNSUPPORTED;
+    if (cfg && cfg->merge_ways != 0 && cfg->merge_ways != 2 && cfg->merge_ways != 4) return TM_ERR_UNSUPPORTED;
     const size_t E = key_size(kt);
     if (n > 0 && (!aligned(keys, E) || !aligned(tmp_keys, E) ||
                   ((vals || tmp_vals) && (!aligned(vals, vs) || !aligned(tmp_vals, vs)))))

@@ -1,0 +1,6 @@
+// Four-run tile-engine kernels (fused merge-sort rounds) for int32_t keys.
+#include "tm_engine4_launch.cuh"
+
+namespace pmerge {
+template tm_status launch_engine4<int32_t>(const Engine4Args&, int, const tm_config*, cudaStream_t);
+}  // namespace pmerge

@@ -44,7 +44,7 @@ class TmConfig(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("stages", ctypes.c_int32), ("split", ctypes.c_int32),
                 ("wait_ms", ctypes.c_int32), ("test_drop_tile", ctypes.c_int32), ("unfused", ctypes.c_int32),
                 ("partition", ctypes.c_int32), ("payload_bytes", ctypes.c_int32), ("trace", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("merge_ways", ctypes.c_int32)]
 
 
 class TmError(RuntimeError):
@@ -378,7 +378,7 @@ def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream
 # ---------------------------------------------------------------------------
 
 def _cfg_dict(c: TmConfig) -> dict:
-    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_ if f != "reserved"}
+    return {f: int(getattr(c, f)) for f, _ in TmConfig._fields_}
 
 
 def tm_merge_batched_workspace_size(num_pairs: int, total_a: int, total_b: int, cfg=None) -> int:

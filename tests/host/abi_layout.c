@@ -23,7 +23,7 @@ int main(void)
     FIELD(tm_config, partition);
     FIELD(tm_config, payload_bytes);
     FIELD(tm_config, trace);
-    FIELD(tm_config, reserved);
+    FIELD(tm_config, merge_ways);
     printf("sizeof %zu\n", sizeof(tm_config));
     return 0;
 }

@@ -177,6 +177,10 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
         cb = tm.TmConfig(payload_bytes=bad)
         assert lib.tm_merge(0, k8, v4, 10, k8, v4, 10, k8, v4, P(256), 1 << 20, ctypes.byref(cb), None) == UNS
         assert lib.tm_merge_sort(0, k8, v4, 10, k8, v4, P(256), 1 << 30, ctypes.byref(cb), None) == UNS
+    # runs merged per sort pass: 2 or 4 (0: the default)
+    for ways in (1, 3, 8, -2):
+        cw = tm.TmConfig(merge_ways=ways)
+        assert lib.tm_merge_sort(0, k8, v4, 10, k8, v4, P(256), 1 << 30, ctypes.byref(cw), None) == UNS
     # configurations tm_merge refuses are refused here too (before any device work)
     for bad in ({"partition": tm.TM_PARTITION_DIAGONALS}, {"partition": 7}, {"threads": 64}, {"threads": 384}):
         c = tm.TmConfig(**bad)

@@ -192,6 +192,43 @@ def test_merge_sort_configs(split):
         sort_check(keys, vals, "u64", cfg={"tile": tile, "split": split})
 
 
+@pytest.mark.parametrize("n", [2049, 3 * 1024 + 5, 4096, 4097, 4 * 4096 - 1, 4 * 4096 + 1, 5 * 4096 + 3,
+                               16 * 4096 + 1000])
+@pytest.mark.parametrize("alphabet", [1, 3, 1 << 12])
+def test_fused_sort_rounds_against_the_oracle(n, alphabet):
+    """Two rounds fused into one pass (cfg merge_ways = 4: groups of four
+    runs, some of them partial or empty at the end), with all keys equal,
+    three distinct keys and many: the oracle's stable sort, as with one
+    round per pass."""
+    g = torch.Generator().manual_seed(n + alphabet)
+    keys = torch.randint(0, alphabet, (n,), generator=g, dtype=torch.int64)
+    vals = torch.arange(n, dtype=torch.int32)
+    sort_check(keys, vals, "u64", cfg={"merge_ways": 4})
+    sort_check(keys, vals, "u64")
+
+
+@pytest.mark.parametrize("tile", [1024, 2048, 4096])
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+def test_fused_sort_rounds_tiles_and_key_types(tile, kt):
+    g = torch.Generator().manual_seed(tile)
+    n = (1 << 17) + 12345
+    keys = torch.randint(-300, 300, (n,), generator=g, dtype=torch.int64)
+    keys = {"u64": keys + 300, "u32": (keys + 300).to(torch.int32), "i32": keys.to(torch.int32),
+            "f32": (keys * 0.25).to(torch.float32)}[kt]
+    vals = torch.arange(n, dtype=torch.int32)
+    sort_check(keys, vals, kt, cfg={"tile": tile, "merge_ways": 4})
+
+
+def test_fused_sort_rounds_keys_only():
+    g = torch.Generator().manual_seed(9)
+    n = (1 << 16) + 999
+    keys = torch.randint(0, 1 << 10, (n,), generator=g, dtype=torch.int64)
+    K, V, ws = tm.tm_merge_sort("u64", keys.to(DEV).clone(), None, cfg={"merge_ways": 4})
+    assert V is None and tm.tm_read_status(ws) == 0
+    OK, _ = oracle.merge_sort(to_np(keys, "u64"), np.arange(n, dtype=np.uint32), run=32)
+    assert first_mismatch(to_np(K, "u64"), OK) is None
+
+
 def test_merge_sort_full_size():
     """2**28 u64 keys uniform in [0, 2**24), payload = original index."""
     keys, vals = W.sort_input(DEV)

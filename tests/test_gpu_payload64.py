@@ -82,11 +82,12 @@ def test_payload64_sort(n):
     g = torch.Generator().manual_seed(n + 1)
     keys = torch.randint(0, 1 << 12, (n,), generator=g, dtype=torch.int64)
     tags = W.payload(0, n, "cpu")
-    K, Vw, ws = tm.tm_merge_sort("u64", keys.to(DEV).clone(), W.widen_payload(tags).to(DEV))
-    assert tm.tm_read_status(ws) == 0
     OK, OV = oracle.merge_sort(to_np(keys, "u64"), vals_np(tags), run=32)
-    assert first_mismatch(to_np(K, "u64"), OK) is None
-    assert first_mismatch(Vw.cpu().numpy().view(np.uint64), wide_np(OV)) is None
+    for cfg in (None, {"merge_ways": 4}):
+        K, Vw, ws = tm.tm_merge_sort("u64", keys.to(DEV).clone(), W.widen_payload(tags).to(DEV), cfg=cfg)
+        assert tm.tm_read_status(ws) == 0
+        assert first_mismatch(to_np(K, "u64"), OK) is None
+        assert first_mismatch(Vw.cpu().numpy().view(np.uint64), wide_np(OV)) is None
 
 
 def test_payload64_large_merge_full_size():
