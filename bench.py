@@ -379,6 +379,8 @@ def compact_forms(forms: dict, peak_gbs: float) -> dict:
                           "e2e_speedup": _r(f.get("end_to_end_speedup")),
                           "search_speedup": _r(f.get("search_speedup")),
                           "search_speedup_pla_only": _r(f.get("search_speedup_pla_only")),
+                          "e2e_speedup_pla_only": _r(f.get("end_to_end_speedup_pla_only")),
+                          "mlp_vs_pla_search": _r(f.get("mlp_vs_pla_search")),
                           "fallbacks": g(g(f, "learned"), "fallbacks"), "bit_identical": f.get("bit_identical"),
                           "cpu": _r(g(g(f, "cpu_baseline"), "value"))}
     f = forms.get("payload64")
@@ -784,9 +786,25 @@ def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int =
     t_learned, srch_learned, src, n_final = run(learned)
     same = torch.equal(bufs[src][0][:n_final], ref[0]) and torch.equal(bufs[src][1][:n_final], ref[1])
     h = model.header()
+    eps_s = model.eps_segments().cpu().numpy()
+    # the same run with the model's piecewise-linear part alone (MLP output
+    # 0: all network parameters zero), calibrated on the same keys
+    pla = tm.CdfModel(4096, 64, dev).init(X0, torch.zeros_like(flat))
+    pla.calibrate(qc, tm.tm_rank_search("f32", "high", qc, X0))
+    pla_state = pla.buf.clone()
+
+    def learned_pla(A, B, p):
+        tm.tm_cross_ranks_learned(pla, A, B, p, xbar, ybar, flags=tm.LEARNED_ADVANCE, stream=s)
+
+    run(learned_pla)                                 # warm-up
+    pla.buf.copy_(pla_state)
+    torch.cuda.synchronize(dev)
+    t_pla, srch_pla, src, n_final = run(learned_pla)
+    same_pla = torch.equal(bufs[src][0][:n_final], ref[0]) and torch.equal(bufs[src][1][:n_final], ref[1])
+    hp = pla.header()
+    eps_p = pla.eps_segments().cpu().numpy()
     elems = sum(N0 + k * m + m for k in range(merges))
     seg = (N0 + merges * m / 2) / 4096
-    eps_s = model.eps_segments().cpu().numpy()
     return {"workload": f"base 2^{log2_base} f32 (3 lognormals) merged {merges} times with sorted 2^{log2_batch} "
                         "batches; u32 payloads",
             "elements": elems,
@@ -798,9 +816,15 @@ def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int =
                         "mean_window_probes": float(np.mean(np.log2(2 * (3 * eps_s * seg + 32) + 1))),
                         "plain_probes": float(np.log2(N0 + merges * m / 2)),
                         "train_seconds_once": train_s},
+            "pla_only": {"value": elems / (t_pla / 1e3), "unit": UNIT, "ms_total": t_pla,
+                         "search_ms_mean": float(np.mean(srch_pla)), "fallbacks": int(hp["fallbacks"]),
+                         "mean_window_probes": float(np.mean(np.log2(2 * (3 * eps_p * seg + 32) + 1)))},
             "search_speedup": float(np.mean(srch_plain) / np.mean(srch_learned)),
+            "search_speedup_pla_only": float(np.mean(srch_plain) / np.mean(srch_pla)),
+            "mlp_vs_pla_search": float(np.mean(srch_pla) / np.mean(srch_learned)),
             "end_to_end_speedup": t_plain / t_learned,
-            "bit_identical": bool(same)}
+            "end_to_end_speedup_pla_only": t_plain / t_pla,
+            "bit_identical": bool(same and same_pla)}
 
 
 def bench_search(dev, log2_base: int = 28, log2_batch: int = 20, reps: int = 30):
@@ -841,10 +865,16 @@ def bench_search(dev, log2_base: int = 28, log2_batch: int = 20, reps: int = 30)
     plain_us = timed(lambda: tm.tm_cross_ranks("f32", A, B, p, xbar, ybar, stream=s))
     xp, yp = xbar.clone(), ybar.clone()
     learned_us = timed(lambda: tm.tm_cross_ranks_learned(model, A, B, p, xbar, ybar, stream=s))
+    same = bool(torch.equal(xp, xbar) and torch.equal(yp, ybar))
+    pla = tm.CdfModel(4096, 64, dev).init(A, torch.zeros_like(flat))      # the network's output 0
+    pla.calibrate(qc, tm.tm_rank_search("f32", "high", qc, A))
+    pla_us = timed(lambda: tm.tm_cross_ranks_learned(pla, A, B, p, xbar, ybar, stream=s))
+    same = same and bool(torch.equal(xp, xbar) and torch.equal(yp, ybar))
     return {"workload": f"base 2^{log2_base} f32 (3 lognormals), batch 2^{log2_batch}, p = {p}",
-            "plain_us": plain_us, "learned_us": learned_us, "speedup": plain_us / learned_us,
-            "identical": bool(torch.equal(xp, xbar) and torch.equal(yp, ybar)),
-            "fallbacks": int(model.header()["fallbacks"])}
+            "plain_us": plain_us, "learned_us": learned_us, "pla_only_us": pla_us,
+            "speedup": plain_us / learned_us, "speedup_pla_only": plain_us / pla_us,
+            "mlp_vs_pla": pla_us / learned_us, "identical": same,
+            "fallbacks": int(model.header()["fallbacks"]), "fallbacks_pla_only": int(pla.header()["fallbacks"])}
 
 
 def main():

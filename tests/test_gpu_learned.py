@@ -169,10 +169,15 @@ def test_gain_of_the_trained_network():
     """What the trained network gains over the method without it.  Plain
     Steps 1-2 bisect the whole base: log2 N probes per search.  The trained
     model proposes each rank and leaves a window of 3 eps_s segment units
-    (eps_s its calibrated error in the key's segment, times 3): far fewer probes, every
-    answer still exact.  Against its own piecewise-linear part alone (MLP
-    output 0), training lowers the objective (mean squared residual); the
-    per-segment maximum errors, which set the windows, are printed."""
+    (eps_s its calibrated error in the key's segment): far fewer probes,
+    every answer still exact.  Against its own piecewise-linear part alone
+    (MLP output 0, calibrated the same way), training lowers the objective
+    (mean squared residual) but not the windows: the residual that sets a
+    segment's maximum error is the sampling noise of the base inside the
+    segment, which a smooth function of (position in segment, segment
+    index) cannot predict.  Asserted: the network's mean window is within a
+    quarter probe of the piecewise-linear part's (it gains no probes, and
+    costs none), and both answer every search of a merge exactly."""
     N = 1 << 24
     X, Xv, q, labels, model, flat = train_lsm_model(N, S=4096, H=64, Q=1 << 18, steps=400)
     zero = torch.zeros(model.P, dtype=torch.float32, device=DEV)
@@ -190,12 +195,14 @@ def test_gain_of_the_trained_network():
           f"mlp {w_mlp.mean():.2f}")
     assert loss_mlp.item() < loss_pla.item()
     assert w_mlp.mean() < np.log2(N) - 10
-    # the learned search answers every query of a merge exactly, with few fallbacks
+    assert abs(w_mlp.mean() - w_pla.mean()) < 0.25
+    # both answer every query of a merge exactly, with few fallbacks
     B, Bv = W.lsm_batch(0, DEV, size=1 << 20, base_n=N)
     p = tm.tm_merge_blocks(N, B.numel())
-    xl, yl = tm.tm_cross_ranks_learned(model, X, B, p)
     xp, yp = tm.tm_cross_ranks("f32", X, B, p)
-    assert torch.equal(xl, xp) and torch.equal(yl, yp)
-    h = model.header()
-    print(f"fallbacks {h['fallbacks']} of {h['learned']} learned searches")
-    assert h["fallbacks"] <= 0.01 * h["learned"]
+    for m_ in (model, pla):
+        xl, yl = tm.tm_cross_ranks_learned(m_, X, B, p)
+        assert torch.equal(xl, xp) and torch.equal(yl, yp)
+        h = m_.header()
+        print(f"fallbacks {h['fallbacks']} of {h['learned']} learned searches")
+        assert h["fallbacks"] <= 0.01 * h["learned"]
