@@ -316,6 +316,25 @@ TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64
                                void* tmp_keys, uint32_t* tmp_vals, void* workspace, size_t workspace_bytes,
                                const tm_config* cfg, tm_stream_t stream);
 
+/* Segmented stable sort: num_segments independent segments of one array,
+ * segment q = (keys, vals)[seg_offsets[q], seg_offsets[q+1]), each sorted
+ * stably by key (Section 3's merge sort inside every segment: runs of at
+ * most 1024 elements that never cross a segment boundary, then rounds that
+ * merge each segment's neighbouring runs pairwise, one batched merge per
+ * round; a segment already sorted is copied).  seg_offsets is HOST memory
+ * (num_segments + 1 int64, from 0, non-decreasing, ending at n): the rounds
+ * are planned on the host and their descriptors copied into the workspace
+ * from pageable host memory, so this call is not graph-capturable.
+ * Invalid offsets return TM_ERR_INVALID.  Passes alternate between (keys,
+ * vals) and (tmp_keys, tmp_vals); the result ends in (keys, vals).  The
+ * paper treats one array; independent segments are this library's. */
+TM_API size_t tm_merge_sort_segmented_workspace_size(int64_t n, const int64_t* seg_offsets, int64_t num_segments,
+                                                     const tm_config* cfg);
+TM_API tm_status tm_merge_sort_segmented(tm_key_type kt, void* keys, uint32_t* vals, int64_t n,
+                                         const int64_t* seg_offsets, int64_t num_segments, void* tmp_keys,
+                                         uint32_t* tmp_vals, void* workspace, size_t workspace_bytes,
+                                         const tm_config* cfg, tm_stream_t stream);
+
 /* Autotuner (not in the paper): runs tm_merge_batched (resp. tm_merge_sort on
  * a fresh device copy of src into keys/vals per trial) once per candidate
  * configuration -- tile {1024, 2048, 4096} x threads {128, 256} x stages

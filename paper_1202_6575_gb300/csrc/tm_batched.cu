@@ -30,15 +30,22 @@ static tm_status launch_status() {
 }
 
 // A set of pairs: either CSR offsets (pair k merges A[a_off[k]..a_off[k+1])
-// with B[b_off[k]..b_off[k+1]) into C from a_off[k] + b_off[k]), or uniform
-// runs of one array (pair k merges the sorted runs [2k*run, (2k+1)*run) and
-// [(2k+1)*run, (2k+2)*run) of X, clipped to `total`, into C from 2k*run).
+// with B[b_off[k]..b_off[k+1]) into C from a_off[k] + b_off[k]), or
+// explicit runs of one array (pair k merges X[a0, a0+n) with the run right
+// after it, X[a0+n, a0+n+m), into C from a0; (a0, n, m) = pdesc[3k..3k+2]),
+// or uniform runs of one array (pair k merges the sorted runs [2k*run,
+// (2k+1)*run) and [(2k+1)*run, (2k+2)*run) of X, clipped to `total`, into C
+// from 2k*run).
 struct PairSet {
     int64_t num_pairs;
     const int64_t* a_off;
     const int64_t* b_off;
-    int64_t run, total;            // uniform mode when a_off == nullptr
+    const int64_t* pdesc;          // explicit mode
+    int64_t run, total;            // uniform mode when a_off == pdesc == nullptr
     int64_t p_uniform;             // blocks per pair in uniform mode
+
+    // Per-pair block counts vary (CSR and explicit modes): they are scanned.
+    __host__ __device__ __forceinline__ bool scanned() const { return a_off != nullptr || pdesc != nullptr; }
 
     __device__ __forceinline__ void get(int64_t k, int64_t& a0, int64_t& n, int64_t& b0, int64_t& m,
                                         int64_t& c0) const {
@@ -46,6 +53,10 @@ struct PairSet {
             a0 = a_off[k]; n = a_off[k + 1] - a0;
             b0 = b_off[k]; m = b_off[k + 1] - b0;
             c0 = a0 + b0;
+        } else if (pdesc) {
+            a0 = pdesc[3 * k]; n = pdesc[3 * k + 1]; m = pdesc[3 * k + 2];
+            b0 = a0 + n;
+            c0 = a0;
         } else {
             a0 = 2 * k * run;
             n = total - a0 < run ? total - a0 : run;
@@ -202,7 +213,7 @@ __device__ __forceinline__ int64_t pair_of(const int64_t* base, int64_t num, int
 // Maps a global (search or plan) thread index to (pair, local index).
 __device__ __forceinline__ bool locate(const PairSet& ps, const PairBases& pb, int64_t t, int64_t& k,
                                        int64_t& local, int64_t& p) {
-    if (ps.a_off) {
+    if (ps.scanned()) {
         if (t >= __ldg(pb.search_base + ps.num_pairs)) return false;
         k = pair_of(pb.search_base, ps.num_pairs, t);
         local = t - __ldg(pb.search_base + k);
@@ -227,7 +238,7 @@ struct PairWin { int64_t kf; int cnt; };           // cnt staged bases; 0: not s
 __device__ __forceinline__ PairWin stage_pair_window(const PairSet& ps, const PairBases& pb, int64_t total_threads,
                                                      int64_t* sb) {
     PairWin w{0, 0};
-    if (!ps.a_off) return w;                           // uniform pairs: closed form, the same for every CTA
+    if (!ps.scanned()) return w;                       // uniform pairs: closed form, the same for every CTA
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
     const int64_t all = __ldg(pb.search_base + ps.num_pairs);
     const int64_t tot = all < total_threads ? all : total_threads;
@@ -247,7 +258,7 @@ __device__ __forceinline__ PairWin stage_pair_window(const PairSet& ps, const Pa
 // locate() through the staged window when there is one.
 __device__ __forceinline__ bool locate_in(const PairSet& ps, const PairBases& pb, const PairWin& w,
                                           const int64_t* sb, int64_t t, int64_t& k, int64_t& local, int64_t& p) {
-    if (ps.a_off && w.cnt) {
+    if (ps.scanned() && w.cnt) {
         if (t >= sb[w.cnt - 1]) return false;          // past the last pair's searches
         int lo = 0, len = w.cnt - 1;                    // last i <= cnt-2 with sb[i] <= t
         while (len > 0) {
@@ -263,11 +274,11 @@ __device__ __forceinline__ bool locate_in(const PairSet& ps, const PairBases& pb
 }
 
 __device__ __forceinline__ int64_t rank_base_of(const PairSet& ps, const PairBases& pb, int64_t k) {
-    return ps.a_off ? __ldg(pb.rank_base + k) : k * (ps.p_uniform + 1);
+    return ps.scanned() ? __ldg(pb.rank_base + k) : k * (ps.p_uniform + 1);
 }
 
 __device__ __forceinline__ int64_t item_base_of(const PairSet& ps, const PairBases& pb, int64_t k) {
-    return ps.a_off ? __ldg(pb.item_base + k) : k * 2 * ps.p_uniform;
+    return ps.scanned() ? __ldg(pb.item_base + k) : k * 2 * ps.p_uniform;
 }
 
 // Steps 1-2 of every pair.
@@ -390,7 +401,7 @@ static tm_status run_pairs(const PairSet& ps, const BatchedWs& w, int64_t total_
     const int64_t total = total_a + total_b;
     PairBases pb{w.search_base, w.rank_base, w.item_base, w.cta_pair};
     int64_t threads;                               // upper bound of sum 2 p_k
-    if (ps.a_off) {
+    if (ps.scanned()) {
         const int64_t blocks = (ps.num_pairs + 255) / 256;
         pair_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(ps, tile, w.search_base, w.rank_base, w.item_base,
                                                           w.part, blocks);
@@ -463,15 +474,18 @@ constexpr int kSortRun = 1024;
 constexpr int kSortThreads = 128;
 constexpr int kSortVT = 9;
 
+// rdesc (optional): run b is X[rdesc[2b], rdesc[2b] + rdesc[2b+1]) (at most
+// kSortRun elements); without it run b is X[b kSortRun, ...) clipped to n.
 template <typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads)
 run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __restrict__ out_k,
-                V* __restrict__ out_v, int64_t n) {
+                V* __restrict__ out_v, int64_t n, const int64_t* __restrict__ rdesc = nullptr) {
     __shared__ K sk[kSortRun + 1];                    // + 1: the merge step reads one past a run
     __shared__ V sv[kSortRun];
     const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kSortRun;
-    const int len = (int)(n - base < kSortRun ? n - base : kSortRun);
+    const int64_t base = rdesc ? __ldg(rdesc + 2 * blockIdx.x) : (int64_t)blockIdx.x * kSortRun;
+    const int64_t rl = rdesc ? __ldg(rdesc + 2 * blockIdx.x + 1) : n - base;
+    const int len = (int)(rl < kSortRun ? (rl > 0 ? rl : 0) : kSortRun);
     for (int i = t; i < len; i += kSortThreads) {      // no payloads (keys-only sort): sv unused
         sk[i] = in_k[base + i];
         if (in_v) sv[i] = in_v[base + i];
@@ -833,6 +847,116 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
 }
 
 // ---------------------------------------------------------------------------
+// Segmented stable merge sort: independent segments of one array
+// ---------------------------------------------------------------------------
+// Runs of at most 1024 elements inside each segment (a run never crosses a
+// segment boundary), then rounds of width w = 1024, 2048, ...: in every
+// round each segment's neighbouring runs are merged pairwise (a last
+// unpaired run, or a segment already sorted, is a pair with an empty second
+// run: a copy).  The plan is made on the host from the host's segment
+// offsets; every round is one batched merge over explicit pairs.
+
+struct SegPlan {
+    std::vector<int64_t> runs;          // (start, length) per run
+    std::vector<int64_t> pairs;         // (a0, n, m) per pair, the rounds one after another
+    std::vector<int64_t> round_first;   // first pair of every round, then the total
+    int64_t max_pairs = 0;
+};
+
+// false when the offsets are not 0 = off[0] <= ... <= off[segs] = n.
+static bool seg_plan(const int64_t* off, int64_t segs, int64_t n, SegPlan& P) {
+    if (segs < 0 || (segs > 0 && off == nullptr)) return false;
+    if (segs == 0) return n == 0;
+    if (off[0] != 0 || off[segs] != n) return false;
+    int64_t maxlen = 0;
+    for (int64_t q = 0; q < segs; ++q) {
+        if (off[q + 1] < off[q]) return false;
+        maxlen = off[q + 1] - off[q] > maxlen ? off[q + 1] - off[q] : maxlen;
+        for (int64_t a = off[q]; a < off[q + 1]; a += kSortRun) {
+            P.runs.push_back(a);
+            P.runs.push_back(off[q + 1] - a < kSortRun ? off[q + 1] - a : kSortRun);
+        }
+    }
+    for (int64_t w = kSortRun; w < maxlen; w *= 2) {
+        const int64_t first = (int64_t)P.pairs.size() / 3;
+        P.round_first.push_back(first);
+        for (int64_t q = 0; q < segs; ++q) {
+            for (int64_t a0 = off[q]; a0 < off[q + 1]; a0 += 2 * w) {
+                const int64_t na = off[q + 1] - a0 < w ? off[q + 1] - a0 : w;
+                const int64_t rest = off[q + 1] - a0 - na;
+                P.pairs.push_back(a0);
+                P.pairs.push_back(na);
+                P.pairs.push_back(rest < w ? rest : w);
+            }
+        }
+        const int64_t cnt = (int64_t)P.pairs.size() / 3 - first;
+        if (cnt > P.max_pairs) P.max_pairs = cnt;
+    }
+    P.round_first.push_back((int64_t)P.pairs.size() / 3);
+    return true;
+}
+
+// Workspace: the batched layout for the largest round, then the run and
+// pair descriptors.
+static BatchedWs seg_ws_layout(void* base, const SegPlan& P, int64_t n, int64_t tile, int64_t** rd, int64_t** pd) {
+    BatchedWs w = batched_ws_layout(base, P.max_pairs, 2 * n, tile);
+    uint8_t* b = static_cast<uint8_t*>(base);
+    size_t o = w.bytes;
+    if (rd) *rd = reinterpret_cast<int64_t*>(b + o);
+    o += align_up(P.runs.size() * 8, 256);
+    if (pd) *pd = reinterpret_cast<int64_t*>(b + o);
+    o += align_up(P.pairs.size() * 8, 256);
+    w.bytes = o;
+    return w;
+}
+
+template <typename K, typename V>
+static tm_status sort_segmented_v(void* keys, void* vals, int64_t n, void* tmp_keys, void* tmp_vals,
+                                  const SegPlan& P, void* ws, const tm_config* cfg, cudaStream_t s) {
+    const int64_t tile = tile_of(cfg);
+    int64_t *rd = nullptr, *pd = nullptr;
+    BatchedWs w = seg_ws_layout(ws, P, n, tile, &rd, &pd);
+    if (const cudaError_t e_ = cudaMemsetAsync(w.control, 0, 16, s); e_ != cudaSuccess) return cuda_failed(e_);
+    if (n == 0) return TM_OK;
+    // descriptors from pageable host memory (staged by the runtime before the call returns)
+    if (const cudaError_t e_ = cudaMemcpyAsync(rd, P.runs.data(), P.runs.size() * 8, cudaMemcpyHostToDevice, s);
+        e_ != cudaSuccess)
+        return cuda_failed(e_);
+    if (!P.pairs.empty()) {
+        if (const cudaError_t e_ = cudaMemcpyAsync(pd, P.pairs.data(), P.pairs.size() * 8, cudaMemcpyHostToDevice, s);
+            e_ != cudaSuccess)
+            return cuda_failed(e_);
+    }
+    K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
+    V* bufv[2] = {static_cast<V*>(vals), static_cast<V*>(tmp_vals)};
+    const int rounds = (int)P.round_first.size() - 1;
+    int src = (rounds % 2 == 0) ? 0 : 1;
+    const int64_t runs = (int64_t)P.runs.size() / 2;
+    if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    run_sort_kernel<K, V><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n, rd);
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
+    for (int r = 0; r < rounds; ++r) {
+        PairSet ps{};
+        ps.num_pairs = P.round_first[r + 1] - P.round_first[r];
+        ps.pdesc = pd + 3 * P.round_first[r];
+        const int dst = src ^ 1;
+        tm_status st = run_pairs<K>(ps, w, n, n, bufk[src], bufv[src], bufk[src], bufv[src], bufk[dst], bufv[dst],
+                                    (int)sizeof(V), tile, -1, cfg, s);
+        if (st != TM_OK) return st;
+        src = dst;
+    }
+    return TM_OK;
+}
+
+template <typename K>
+static tm_status sort_segmented_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
+                                      const SegPlan& P, void* ws, const tm_config* cfg, cudaStream_t s) {
+    if (payload_size(cfg) == 8)
+        return sort_segmented_v<K, uint64_t>(keys, vals, n, tmp_keys, tmp_vals, P, ws, cfg, s);
+    return sort_segmented_v<K, uint32_t>(keys, vals, n, tmp_keys, tmp_vals, P, ws, cfg, s);
+}
+
+// ---------------------------------------------------------------------------
 // Autotuner: times candidate configurations on the caller's data with CUDA
 // events and remembers the fastest per (key type, size bucket, operation).
 // ---------------------------------------------------------------------------
@@ -945,6 +1069,39 @@ tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64_t n, v
         case TM_KEY_I32: return sort_typed<int32_t>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
         case TM_KEY_U64: return sort_typed<uint64_t>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
         case TM_KEY_F32: return sort_typed<float>(keys, vals, n, tmp_keys, tmp_vals, workspace, cfg, s);
+    }
+    return TM_ERR_UNSUPPORTED;
+}
+
+size_t tm_merge_sort_segmented_workspace_size(int64_t n, const int64_t* seg_offsets, int64_t num_segments,
+                                              const tm_config* cfg) {
+    SegPlan P;
+    if (n < 0 || !seg_plan(seg_offsets, num_segments, n, P)) return 0;
+    return seg_ws_layout(nullptr, P, n, tile_of(cfg), nullptr, nullptr).bytes;
+}
+
+tm_status tm_merge_sort_segmented(tm_key_type kt, void* keys, uint32_t* vals, int64_t n,
+                                  const int64_t* seg_offsets, int64_t num_segments, void* tmp_keys,
+                                  uint32_t* tmp_vals, void* workspace, size_t workspace_bytes, const tm_config* cfg,
+                                  tm_stream_t stream) {
+    if (n < 0) return TM_ERR_INVALID;
+    const int vs = payload_size(cfg);
+    if (kt < TM_KEY_U32 || kt > TM_KEY_F32 || vs < 0) return TM_ERR_UNSUPPORTED;
+    const size_t E = key_size(kt);
+    if (n > 0 && (!aligned(keys, E) || !aligned(tmp_keys, E) ||
+                  ((vals || tmp_vals) && (!aligned(vals, vs) || !aligned(tmp_vals, vs)))))
+        return TM_ERR_INVALID;
+    SegPlan P;
+    if (!seg_plan(seg_offsets, num_segments, n, P)) return TM_ERR_INVALID;
+    if (!workspace || !aligned(workspace, 256) ||
+        workspace_bytes < seg_ws_layout(nullptr, P, n, tile_of(cfg), nullptr, nullptr).bytes)
+        return TM_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (kt) {
+        case TM_KEY_U32: return sort_segmented_typed<uint32_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
+        case TM_KEY_I32: return sort_segmented_typed<int32_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
+        case TM_KEY_U64: return sort_segmented_typed<uint64_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
+        case TM_KEY_F32: return sort_segmented_typed<float>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
     }
     return TM_ERR_UNSUPPORTED;
 }

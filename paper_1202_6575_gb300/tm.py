@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -76,6 +77,8 @@ _SIGNATURES = {
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "tm_merge_phase_times": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
+    "tm_merge_sort_segmented_workspace_size": (_SZ, [_I64, _P, _I64, _P]),
+    "tm_merge_sort_segmented": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P, _P]),
     "tm_merge_batched_workspace_size": (_SZ, [_I64, _I64, _I64, _P]),
     "tm_merge_batched": (ctypes.c_int, [ctypes.c_int, _I64, _P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P, _SZ,
                                         _P, _P]),
@@ -434,6 +437,50 @@ def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=N
                                 _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", ANY_PAYLOAD_DTYPES),
                                 _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg), _stream(stream))
     _check(code, "tm_merge_sort")
+    return keys, vals, workspace
+
+
+def _host_offsets(seg_offsets) -> np.ndarray:
+    """Segment offsets as a contiguous host int64 array (list, numpy array or
+    CPU tensor)."""
+    if isinstance(seg_offsets, torch.Tensor):
+        if seg_offsets.is_cuda:
+            raise ValueError("seg_offsets are read on the host: pass a CPU tensor, list or numpy array")
+        seg_offsets = seg_offsets.numpy()
+    return np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+
+
+def tm_merge_sort_segmented_workspace_size(n: int, seg_offsets, cfg=None) -> int:
+    off = _host_offsets(seg_offsets)
+    return int(load().tm_merge_sort_segmented_workspace_size(n, off.ctypes.data_as(ctypes.c_void_p),
+                                                             len(off) - 1, _cfg(cfg)))
+
+
+def tm_merge_sort_segmented(kt: str, keys, vals, seg_offsets, tmp_keys=None, tmp_vals=None, workspace=None,
+                            cfg=None, stream=None):
+    """Stable sort of every segment [seg_offsets[q], seg_offsets[q+1]) of
+    (keys, vals) in place; seg_offsets on the host.  Returns (keys, vals,
+    workspace)."""
+    kd = TORCH_KEY_DTYPES[kt]
+    n = keys.numel()
+    off = _host_offsets(seg_offsets)
+    if tmp_keys is None:
+        tmp_keys = torch.empty_like(keys)
+    if tmp_vals is None and vals is not None:
+        tmp_vals = torch.empty_like(vals)
+    cfg = _payload_cfg(cfg, vals, tmp_vals)
+    if workspace is None:
+        size = tm_merge_sort_segmented_workspace_size(n, off, cfg)
+        if size == 0:
+            raise TmError(TM_ERR_INVALID, "tm_merge_sort_segmented_workspace_size")
+        workspace = new_workspace(size, keys.device)
+    P = ANY_PAYLOAD_DTYPES
+    code = load().tm_merge_sort_segmented(_kt(kt), _dev(keys, "keys", kd), _dev(vals, "vals", P), n,
+                                          off.ctypes.data_as(ctypes.c_void_p), len(off) - 1,
+                                          _dev(tmp_keys, "tmp_keys", kd), _dev(tmp_vals, "tmp_vals", P),
+                                          _dev(workspace, "workspace"), workspace.numel(), _cfg(cfg),
+                                          _stream(stream))
+    _check(code, "tm_merge_sort_segmented")
     return keys, vals, workspace
 
 

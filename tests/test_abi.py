@@ -276,3 +276,28 @@ def test_binding_derives_the_payload_width_from_the_tensors():
         tm._payload_cfg({"payload_bytes": 4}, v64)
     with pytest.raises(ValueError):
         tm._payload_cfg(tm.TmConfig(payload_bytes=8), v32)
+
+
+def test_segmented_sort_offsets_and_sizing_on_the_host(lib):
+    """The segmented sort plans on the host: invalid offsets are refused
+    before anything reaches a device, and the workspace grows with the
+    number of rounds and pairs."""
+    import numpy as np
+    P = ctypes.c_void_p
+    INV = tm.TM_ERR_INVALID
+
+    def offs(v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+        return a, a.ctypes.data_as(P)
+
+    for bad, n in (([1, 5], 5), ([0, 4], 5), ([0, 3, 2, 5], 5), ([0, 6], 5)):
+        a, ptr = offs(bad)
+        assert lib.tm_merge_sort_segmented_workspace_size(n, ptr, len(a) - 1, None) == 0
+        assert lib.tm_merge_sort_segmented(0, P(256), P(512), n, ptr, len(a) - 1, P(768), P(1024), P(4096),
+                                           1 << 30, None, None) == INV
+    a1, p1 = offs([0, 1000, 1000, 5000])
+    a2, p2 = offs([0, 1000, 1000, 1 << 20])
+    s1 = lib.tm_merge_sort_segmented_workspace_size(5000, p1, 3, None)
+    s2 = lib.tm_merge_sort_segmented_workspace_size(1 << 20, p2, 3, None)
+    assert 0 < s1 < s2
+    assert tm.tm_merge_sort_segmented_workspace_size(5000, [0, 1000, 1000, 5000]) == s1
