@@ -621,6 +621,7 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
     ms = e0.elapsed_time(e1) / steps
     assert tm.tm_read_status(ws, stream=s) == 0
     ms_plain = None
+    same = None
     if with_plain:
         # plain form: one tm_merge per pair (host loop, one stream)
         ho_a, ho_b = a_off.cpu().tolist(), b_off.cpu().tolist()
@@ -631,8 +632,12 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
                 c0 = a0 + b0
                 L = (a1 - a0) + (b1 - b0)
                 tm.tm_merge("u64", A[a0:a1], Av[a0:a1], B[b0:b1], Bv[b0:b1], C[c0:c0 + L], Cv[c0:c0 + L], wsp, stream=s)
+        ref = (C.clone(), Cv.clone())                 # the graph's output
+        C.fill_(-1)
+        Cv.fill_(-1)
         plain()
         s.synchronize()
+        same = bool(torch.equal(ref[0], C) and torch.equal(ref[1], Cv))
         e0.record(s)
         plain()
         e1.record(s)
@@ -646,7 +651,8 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
             "config": best, "gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0],
             "plain_per_pair_tm_merge": None if ms_plain is None else {"value": total / (ms_plain / 1e3),
                                                                        "ms": ms_plain, "calls": pairs},
-            "speedup_vs_plain": None if ms_plain is None else ms_plain / ms}
+            "speedup_vs_plain": None if ms_plain is None else ms_plain / ms,
+            "bit_exact": same}
 
 
 def bench_sort(dev, steps: int = 3, cfg=None):
@@ -690,6 +696,14 @@ def bench_sort(dev, steps: int = 3, cfg=None):
         utimes.append(e0.elapsed_time(e1))
     assert tm.tm_read_status(ws, stream=s) == 0
     same = bool(torch.equal(ref[0], keys) and torch.equal(ref[1], vals))
+    # the stable order at full size: keys non-decreasing, and on equal keys
+    # the payloads (original indices) increasing
+    k0, k1, v0, v1 = ref[0][:-1], ref[0][1:], ref[1][:-1], ref[1][1:]
+    stable = bool(((k0 < k1) | ((k0 == k1) & (v0 < v1))).all())
+    idx = ref[1].long()                               # a permutation, each key its input's
+    stable = stable and bool(torch.equal(torch.sort(idx).values, torch.arange(n, device=dev))) and \
+        bool(torch.equal(ref[0], src_k[idx]))
+    del k0, k1, v0, v1, idx
     ums = float(np.median(utimes[1:]))
     rounds = 0
     r = 1024
@@ -702,7 +716,7 @@ def bench_sort(dev, steps: int = 3, cfg=None):
             "config": best, "passes_gbs": moved / (ms / 1e3) / 1e9,
             "frac_of_hbm": moved / (ms / 1e3) / 1e9 / measured_peaks()[0],
             "four_way_ms": ums, "four_way_passes": 1 + rounds // 2 + rounds % 2,
-            "four_way_bit_exact": same}
+            "four_way_bit_exact": same, "bit_exact": bool(stable and same)}
 
 
 def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int = 20):
