@@ -3,9 +3,11 @@ keys (three lognormals, payload = insertion number) merged 256 times with
 sorted batches of 2^20 keys of the same mixture, the base on the A side and
 the model's knot ranks advanced by every merge (base' = merge(base, batch)).
 Every merge's cross ranks, the learned ones (the B-block starts searched in
-the base) included, equal the plain search's; the merged base equals the
-oracle's two-pointer merge on the first merge, every 16th and the last; the
-model falls back to the full search on at most 1 % of its searches."""
+the base) included, equal the plain search's (all 256 merges); the merged
+base equals the oracle's two-pointer merge on the first merge, every 16th
+and the last (17 of the 256: the oracle's CPU merge of a 2^28-element base
+is the slow part); the model falls back to the full search on at most 1 %
+of its searches."""
 import pytest
 import torch
 
