@@ -386,6 +386,10 @@ def compact_forms(forms: dict, peak_gbs: float) -> dict:
     f = forms.get("payload64")
     if isinstance(f, dict) and "error" not in f:
         out["payload64"] = {"value": _r(f.get("value")), "ms": _r(f.get("ms")), "frac_of_hbm": _r(f.get("frac_of_hbm"))}
+    f = forms.get("segmented_sort")
+    if isinstance(f, dict) and "error" not in f:
+        out["segmented_sort"] = {"value": _r(f.get("value")), "ms": _r(f.get("ms")),
+                                 "frac_of_hbm": _r(f.get("frac_of_hbm")), "bit_exact": f.get("bit_exact")}
     f = forms.get("partition_ablation")
     if isinstance(f, dict) and "error" not in f:
         out["partition_ablation"] = {"equal_output_over_blocks": _r(f.get("equal_output_over_blocks"))}
@@ -719,6 +723,58 @@ def bench_sort(dev, steps: int = 3, cfg=None):
             "four_way_bit_exact": same, "bit_exact": bool(stable and same)}
 
 
+def bench_segmented(dev, steps: int = 3):
+    """Segmented stable sort: 65,536 segments whose lengths are those of the
+    batched workload's pairs (n_k + m_k, each side log-uniform in [1, 2**16]),
+    u64 keys uniform in [0, 2**20) (unsorted) with u32 payloads = index; one
+    tm_merge_sort_segmented call, median of `steps` after one warm call.
+    Checked at full size: inside every segment the keys are non-decreasing
+    and equal keys keep their input order, and the output is a permutation
+    that never moves an element out of its segment."""
+    from paper_1202_6575_gb300 import tm, workloads as W
+    a_off, A, Av, b_off, B, Bv = W.batched_pairs(dev)
+    del A, Av, B, Bv
+    a_off, b_off = a_off.cpu(), b_off.cpu()
+    lens = (a_off[1:] - a_off[:-1]) + (b_off[1:] - b_off[:-1])
+    offs = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(lens, 0)])
+    n = int(offs[-1])
+    g = torch.Generator(device=dev)
+    g.manual_seed(W.SEED_BASE + 9)
+    src_k = torch.randint(0, 1 << 20, (n,), generator=g, device=dev, dtype=torch.int64)
+    src_v = torch.arange(n, device=dev, dtype=torch.int64).to(torch.int32)
+    keys, vals = torch.empty_like(src_k), torch.empty_like(src_v)
+    tk, tv = torch.empty_like(src_k), torch.empty_like(src_v)
+    ws = tm.new_workspace(tm.tm_merge_sort_segmented_workspace_size(n, offs), dev)
+    times = []
+    for _ in range(steps + 1):
+        keys.copy_(src_k)
+        vals.copy_(src_v)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tm.tm_merge_sort_segmented("u64", keys, vals, offs, tk, tv, ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert tm.tm_read_status(ws) == 0
+    ms = float(np.median(times[1:]))
+    seg = torch.repeat_interleave(torch.arange(lens.numel(), device=dev), lens.to(dev))
+    idx = vals.long()
+    ok = bool(torch.equal(torch.sort(idx).values, torch.arange(n, device=dev))) and \
+        bool(torch.equal(keys, src_k[idx])) and bool(torch.equal(seg[idx], seg))
+    s0, s1, k0, k1, v0, v1 = seg[:-1], seg[1:], keys[:-1], keys[1:], vals[:-1], vals[1:]
+    ok = ok and bool(((s0 != s1) | (k0 < k1) | ((k0 == k1) & (v0 < v1))).all())
+    rounds = 0
+    while (1024 << rounds) < int(lens.max()):
+        rounds += 1
+    moved = n * 24 * (rounds + 1)
+    gbs = moved / (ms / 1e3) / 1e9
+    return {"workload": f"{lens.numel():,} segments (lengths of the batched pairs), {n:,} u64 keys in [0, 2^20) + "
+                        "u32 payloads, unsorted", "elements": n, "value": n / (ms / 1e3), "unit": "sorted elems/s",
+            "ms": ms, "rounds": rounds, "passes_gbs": gbs, "frac_of_hbm": gbs / measured_peaks()[0],
+            "bit_exact": ok}
+
+
 def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int = 20):
     """LSM-style repeated merging: a sorted float32 base of 2**28 keys (3
     lognormals, mu 0/2/5, sigma 0.5) merged `merges` times with sorted
@@ -909,7 +965,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
     ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys",
-                                                   "partition", "payload64"],
+                                                   "partition", "payload64", "segmented"],
                     help="run one form alone (profiling)")
     ap.add_argument("--merges", type=int, default=256, help="learned form: merges (profiling)")
     ap.add_argument("--pairs", type=int, default=65536, help="batched form: pairs (profiling)")
@@ -945,6 +1001,8 @@ def main():
             out = bench_partition(dev)
         elif args.form == "payload64":
             out = bench_payload64(dev)
+        elif args.form == "segmented":
+            out = bench_segmented(dev)
         else:
             out = bench_learned(dev, merges=args.merges, log2_base=args.log2_base)
         print(json.dumps({"form": args.form, **out}), flush=True)
@@ -1146,7 +1204,8 @@ def main():
         torch.cuda.empty_cache()
         forms = {"merge_1m_p1024": bench_small_merge(dev), "batched": bench_batched(dev),
                  "merge_sort": bench_sort(dev), "keys_only": bench_keys_only(dev),
-                 "payload64": bench_payload64(dev), "partition_ablation": bench_partition(dev)}
+                 "payload64": bench_payload64(dev), "segmented_sort": guarded(bench_segmented, dev),
+                 "partition_ablation": bench_partition(dev)}
         torch.cuda.empty_cache()
         forms["learned"] = bench_learned(dev)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -122,6 +122,7 @@ def _full_forms():
         "keys_only": {"uniform_full": {"ms": 1.24, "value": 4.3e11, "gbs": 3460.0, "frac_of_hbm": 0.51},
                       "uniform_1024": {"ms": 0.92, "value": 5.8e11, "gbs": 4660.0, "frac_of_hbm": 0.69}},
         "payload64": {"ms": 1.9, "value": 2.8e11, "gbs": 6780.0, "frac_of_hbm": 1.01, "workload": "w" * 80},
+        "segmented_sort": {"ms": 40.0, "value": 1.9e10, "frac_of_hbm": 0.7, "bit_exact": True, "workload": "w" * 80},
         "partition_ablation": {"blocks": {"total_ms": 8.12, "per_merge_ms": per},
                                "equal_output": {"total_ms": 8.63, "per_merge_ms": per},
                                "equal_output_over_blocks": 1.063},
@@ -155,7 +156,7 @@ def test_compact_line_keeps_every_form_and_stays_short():
     s = json.dumps(c, separators=(",", ":"))
     assert len(s) < 2400, len(s)           # the driver keeps about the last 3000 characters
     for form in ("merge_1m_p1024", "batched", "merge_sort", "keys_only", "learned", "partition_ablation",
-                 "payload64"):
+                 "payload64", "segmented_sort"):
         assert form in c["forms"]
     assert c["forms"]["merge_1m_p1024"]["us"] == 27.1
     assert c["forms"]["merge_1m_p1024"]["phases_us"]["merge"] == 11.0
