@@ -322,9 +322,10 @@ TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64
  * most 1024 elements that never cross a segment boundary, then rounds that
  * merge each segment's neighbouring runs pairwise, one batched merge per
  * round; a segment already sorted is copied).  seg_offsets is HOST memory
- * (num_segments + 1 int64, from 0, non-decreasing, ending at n): the rounds
- * are planned on the host and their descriptors copied into the workspace
- * from pageable host memory, so this call is not graph-capturable.
+ * (num_segments + 1 int64, from 0, non-decreasing, ending at n): the host
+ * counts runs and pairs per round, the offsets are copied into the
+ * workspace from pageable host memory (so this call is not
+ * graph-capturable) and device kernels write the run and pair descriptors.
  * Invalid offsets return TM_ERR_INVALID.  Passes alternate between (keys,
  * vals) and (tmp_keys, tmp_vals); the result ends in (keys, vals).  The
  * paper treats one array; independent segments are this library's. */

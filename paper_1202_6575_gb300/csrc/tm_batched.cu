@@ -857,9 +857,8 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
 // offsets; every round is one batched merge over explicit pairs.
 
 struct SegPlan {
-    std::vector<int64_t> runs;          // (start, length) per run
-    std::vector<int64_t> pairs;         // (a0, n, m) per pair, the rounds one after another
-    std::vector<int64_t> round_first;   // first pair of every round, then the total
+    int64_t segs = 0, runs = 0;
+    std::vector<int64_t> round_pairs;   // pairs of every round
     int64_t max_pairs = 0;
 };
 
@@ -869,76 +868,116 @@ static bool seg_plan(const int64_t* off, int64_t segs, int64_t n, SegPlan& P) {
     if (segs == 0) return n == 0;
     if (off[0] != 0 || off[segs] != n) return false;
     int64_t maxlen = 0;
+    P.segs = segs;
     for (int64_t q = 0; q < segs; ++q) {
-        if (off[q + 1] < off[q]) return false;
-        maxlen = off[q + 1] - off[q] > maxlen ? off[q + 1] - off[q] : maxlen;
-        for (int64_t a = off[q]; a < off[q + 1]; a += kSortRun) {
-            P.runs.push_back(a);
-            P.runs.push_back(off[q + 1] - a < kSortRun ? off[q + 1] - a : kSortRun);
-        }
+        const int64_t len = off[q + 1] - off[q];
+        if (len < 0) return false;
+        maxlen = len > maxlen ? len : maxlen;
+        P.runs += (len + kSortRun - 1) / kSortRun;
     }
     for (int64_t w = kSortRun; w < maxlen; w *= 2) {
-        const int64_t first = (int64_t)P.pairs.size() / 3;
-        P.round_first.push_back(first);
-        for (int64_t q = 0; q < segs; ++q) {
-            for (int64_t a0 = off[q]; a0 < off[q + 1]; a0 += 2 * w) {
-                const int64_t na = off[q + 1] - a0 < w ? off[q + 1] - a0 : w;
-                const int64_t rest = off[q + 1] - a0 - na;
-                P.pairs.push_back(a0);
-                P.pairs.push_back(na);
-                P.pairs.push_back(rest < w ? rest : w);
-            }
-        }
-        const int64_t cnt = (int64_t)P.pairs.size() / 3 - first;
+        int64_t cnt = 0;
+        for (int64_t q = 0; q < segs; ++q) cnt += (off[q + 1] - off[q] + 2 * w - 1) / (2 * w);
+        P.round_pairs.push_back(cnt);
         if (cnt > P.max_pairs) P.max_pairs = cnt;
     }
-    P.round_first.push_back((int64_t)P.pairs.size() / 3);
     return true;
 }
 
-// Workspace: the batched layout for the largest round, then the run and
-// pair descriptors.
-static BatchedWs seg_ws_layout(void* base, const SegPlan& P, int64_t n, int64_t tile, int64_t** rd, int64_t** pd) {
-    BatchedWs w = batched_ws_layout(base, P.max_pairs, 2 * n, tile);
+// Exclusive prefix over the segments of ceil(len_q / unit) (one CTA,
+// rounds of 1024 with a running carry); pre[segs] = the total.
+__global__ void __launch_bounds__(1024)
+seg_prefix_kernel(const int64_t* __restrict__ off, int64_t segs, int64_t unit, int64_t* __restrict__ pre) {
+    int64_t carry = 0;
+    for (int64_t r = 0; r < segs; r += 1024) {
+        const int64_t q = r + threadIdx.x;
+        int64_t v[3] = {q < segs ? (off[q + 1] - off[q] + unit - 1) / unit : 0, 0, 0};
+        int64_t ex[3], tot[3];
+        block_scan3<1024>(v, ex, tot);
+        if (q < segs) pre[q] = carry + ex[0];
+        carry += tot[0];
+    }
+    if (threadIdx.x == 0) pre[segs] = carry;
+}
+
+// Runs of segment q: (start, length) at pre[q]...; thread per segment.
+__global__ void __launch_bounds__(256)
+seg_runs_kernel(const int64_t* __restrict__ off, int64_t segs, const int64_t* __restrict__ pre,
+                int64_t* __restrict__ rdesc) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= segs) return;
+    int64_t o = pre[q];
+    for (int64_t a = off[q]; a < off[q + 1]; a += kSortRun, ++o) {
+        rdesc[2 * o] = a;
+        rdesc[2 * o + 1] = off[q + 1] - a < kSortRun ? off[q + 1] - a : kSortRun;
+    }
+}
+
+// Pairs of segment q in the round of width w: (a0, n, m) at pre[q]...
+__global__ void __launch_bounds__(256)
+seg_pairs_kernel(const int64_t* __restrict__ off, int64_t segs, int64_t w, const int64_t* __restrict__ pre,
+                 int64_t* __restrict__ pdesc) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= segs) return;
+    int64_t o = pre[q];
+    for (int64_t a0 = off[q]; a0 < off[q + 1]; a0 += 2 * w, ++o) {
+        const int64_t na = off[q + 1] - a0 < w ? off[q + 1] - a0 : w;
+        const int64_t rest = off[q + 1] - a0 - na;
+        pdesc[3 * o] = a0;
+        pdesc[3 * o + 1] = na;
+        pdesc[3 * o + 2] = rest < w ? rest : w;
+    }
+}
+
+// Workspace: the batched layout for the largest round, then the segment
+// offsets, a prefix array, the run and the pair descriptors.
+struct SegWs { BatchedWs w; int64_t *off, *pre, *rd, *pd; };
+
+static SegWs seg_ws_layout(void* base, const SegPlan& P, int64_t n, int64_t tile) {
+    SegWs x;
+    x.w = batched_ws_layout(base, P.max_pairs, 2 * n, tile);
     uint8_t* b = static_cast<uint8_t*>(base);
-    size_t o = w.bytes;
-    if (rd) *rd = reinterpret_cast<int64_t*>(b + o);
-    o += align_up(P.runs.size() * 8, 256);
-    if (pd) *pd = reinterpret_cast<int64_t*>(b + o);
-    o += align_up(P.pairs.size() * 8, 256);
-    w.bytes = o;
-    return w;
+    size_t o = x.w.bytes;
+    x.off = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(P.segs + 1) * 8, 256);
+    x.pre = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)(P.segs + 1) * 8, 256);
+    x.rd = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)P.runs * 16, 256);
+    x.pd = reinterpret_cast<int64_t*>(b + o); o += align_up((size_t)P.max_pairs * 24, 256);
+    x.w.bytes = o;
+    return x;
 }
 
 template <typename K, typename V>
 static tm_status sort_segmented_v(void* keys, void* vals, int64_t n, void* tmp_keys, void* tmp_vals,
-                                  const SegPlan& P, void* ws, const tm_config* cfg, cudaStream_t s) {
+                                  const int64_t* host_off, const SegPlan& P, void* ws, const tm_config* cfg,
+                                  cudaStream_t s) {
     const int64_t tile = tile_of(cfg);
-    int64_t *rd = nullptr, *pd = nullptr;
-    BatchedWs w = seg_ws_layout(ws, P, n, tile, &rd, &pd);
+    SegWs x = seg_ws_layout(ws, P, n, tile);
+    BatchedWs& w = x.w;
     if (const cudaError_t e_ = cudaMemsetAsync(w.control, 0, 16, s); e_ != cudaSuccess) return cuda_failed(e_);
     if (n == 0) return TM_OK;
-    // descriptors from pageable host memory (staged by the runtime before the call returns)
-    if (const cudaError_t e_ = cudaMemcpyAsync(rd, P.runs.data(), P.runs.size() * 8, cudaMemcpyHostToDevice, s);
+    // the segment offsets (pageable host memory, staged before the call returns)
+    if (const cudaError_t e_ = cudaMemcpyAsync(x.off, host_off, (size_t)(P.segs + 1) * 8, cudaMemcpyHostToDevice, s);
         e_ != cudaSuccess)
         return cuda_failed(e_);
-    if (!P.pairs.empty()) {
-        if (const cudaError_t e_ = cudaMemcpyAsync(pd, P.pairs.data(), P.pairs.size() * 8, cudaMemcpyHostToDevice, s);
-            e_ != cudaSuccess)
-            return cuda_failed(e_);
-    }
+    const unsigned sg = (unsigned)((P.segs + 255) / 256);
+    seg_prefix_kernel<<<1, 1024, 0, s>>>(x.off, P.segs, kSortRun, x.pre);
+    seg_runs_kernel<<<sg, 256, 0, s>>>(x.off, P.segs, x.pre, x.rd);
+    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
     K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
     V* bufv[2] = {static_cast<V*>(vals), static_cast<V*>(tmp_vals)};
-    const int rounds = (int)P.round_first.size() - 1;
+    const int rounds = (int)P.round_pairs.size();
     int src = (rounds % 2 == 0) ? 0 : 1;
-    const int64_t runs = (int64_t)P.runs.size() / 2;
-    if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
-    run_sort_kernel<K, V><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n, rd);
+    if (P.runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
+    run_sort_kernel<K, V><<<(unsigned)P.runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n, x.rd);
     if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
-    for (int r = 0; r < rounds; ++r) {
+    int64_t wd = kSortRun;
+    for (int r = 0; r < rounds; ++r, wd *= 2) {
+        seg_prefix_kernel<<<1, 1024, 0, s>>>(x.off, P.segs, 2 * wd, x.pre);
+        seg_pairs_kernel<<<sg, 256, 0, s>>>(x.off, P.segs, wd, x.pre, x.pd);
+        if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
         PairSet ps{};
-        ps.num_pairs = P.round_first[r + 1] - P.round_first[r];
-        ps.pdesc = pd + 3 * P.round_first[r];
+        ps.num_pairs = P.round_pairs[r];
+        ps.pdesc = x.pd;
         const int dst = src ^ 1;
         tm_status st = run_pairs<K>(ps, w, n, n, bufk[src], bufv[src], bufk[src], bufv[src], bufk[dst], bufv[dst],
                                     (int)sizeof(V), tile, -1, cfg, s);
@@ -950,10 +989,11 @@ static tm_status sort_segmented_v(void* keys, void* vals, int64_t n, void* tmp_k
 
 template <typename K>
 static tm_status sort_segmented_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_keys, uint32_t* tmp_vals,
-                                      const SegPlan& P, void* ws, const tm_config* cfg, cudaStream_t s) {
+                                      const int64_t* off, const SegPlan& P, void* ws, const tm_config* cfg,
+                                      cudaStream_t s) {
     if (payload_size(cfg) == 8)
-        return sort_segmented_v<K, uint64_t>(keys, vals, n, tmp_keys, tmp_vals, P, ws, cfg, s);
-    return sort_segmented_v<K, uint32_t>(keys, vals, n, tmp_keys, tmp_vals, P, ws, cfg, s);
+        return sort_segmented_v<K, uint64_t>(keys, vals, n, tmp_keys, tmp_vals, off, P, ws, cfg, s);
+    return sort_segmented_v<K, uint32_t>(keys, vals, n, tmp_keys, tmp_vals, off, P, ws, cfg, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1077,7 +1117,7 @@ size_t tm_merge_sort_segmented_workspace_size(int64_t n, const int64_t* seg_offs
                                               const tm_config* cfg) {
     SegPlan P;
     if (n < 0 || !seg_plan(seg_offsets, num_segments, n, P)) return 0;
-    return seg_ws_layout(nullptr, P, n, tile_of(cfg), nullptr, nullptr).bytes;
+    return seg_ws_layout(nullptr, P, n, tile_of(cfg)).w.bytes;
 }
 
 tm_status tm_merge_sort_segmented(tm_key_type kt, void* keys, uint32_t* vals, int64_t n,
@@ -1094,14 +1134,14 @@ tm_status tm_merge_sort_segmented(tm_key_type kt, void* keys, uint32_t* vals, in
     SegPlan P;
     if (!seg_plan(seg_offsets, num_segments, n, P)) return TM_ERR_INVALID;
     if (!workspace || !aligned(workspace, 256) ||
-        workspace_bytes < seg_ws_layout(nullptr, P, n, tile_of(cfg), nullptr, nullptr).bytes)
+        workspace_bytes < seg_ws_layout(nullptr, P, n, tile_of(cfg)).w.bytes)
         return TM_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (kt) {
-        case TM_KEY_U32: return sort_segmented_typed<uint32_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
-        case TM_KEY_I32: return sort_segmented_typed<int32_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
-        case TM_KEY_U64: return sort_segmented_typed<uint64_t>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
-        case TM_KEY_F32: return sort_segmented_typed<float>(keys, vals, n, tmp_keys, tmp_vals, P, workspace, cfg, s);
+        case TM_KEY_U32: return sort_segmented_typed<uint32_t>(keys, vals, n, tmp_keys, tmp_vals, seg_offsets, P, workspace, cfg, s);
+        case TM_KEY_I32: return sort_segmented_typed<int32_t>(keys, vals, n, tmp_keys, tmp_vals, seg_offsets, P, workspace, cfg, s);
+        case TM_KEY_U64: return sort_segmented_typed<uint64_t>(keys, vals, n, tmp_keys, tmp_vals, seg_offsets, P, workspace, cfg, s);
+        case TM_KEY_F32: return sort_segmented_typed<float>(keys, vals, n, tmp_keys, tmp_vals, seg_offsets, P, workspace, cfg, s);
     }
     return TM_ERR_UNSUPPORTED;
 }
