@@ -154,7 +154,7 @@ def test_compact_line_keeps_every_form_and_stays_short():
             "gpu_launches": 4800}
     c = bench.compact_line(line, 6703.8)
     s = json.dumps(c, separators=(",", ":"))
-    assert len(s) < 2400, len(s)           # the driver keeps about the last 3000 characters
+    assert len(s) < 2400, len(s)           # whole inside a log cut to its last 3000 characters
     for form in ("merge_1m_p1024", "batched", "merge_sort", "keys_only", "learned", "partition_ablation",
                  "payload64", "segmented_sort"):
         assert form in c["forms"]
