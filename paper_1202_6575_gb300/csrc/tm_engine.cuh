@@ -72,9 +72,10 @@ struct BlockSplit {
     }
 };
 
-// Named barrier among the consumer warps only (the producer never joins).
-__device__ __forceinline__ void consumer_sync(int nthreads) {
-    asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
+// Named barrier among the consumer warps of one group (the producer never
+// joins); group g uses barrier 1 + g.
+__device__ __forceinline__ void consumer_sync(int nthreads, int id = 1) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
 }
 
 // rank_low(x, X[0..len)) and rank_high(y, Y[0..len2)) in shared memory, as
@@ -482,15 +483,19 @@ __device__ __forceinline__ bool stage_tile(const EngineArgs& g, uint8_t* smem, u
     return true;
 }
 
-// End marker for the consumers after the last fill (lane 0).
-template <int S_IN>
+// End markers for the consumers after the last fill (lane 0): one in each
+// of the next NG fills, so that every consumer group (group j takes the
+// fills j, j + NG, ...) finds one.
+template <int S_IN, int NG = 1>
 __device__ __forceinline__ void stage_end(const EngineArgs& g, uint8_t* smem, uint64_t* full, uint64_t* empty,
                                           int lane, int k) {
     if (lane != 0) return;
-    const int s = k % S_IN;
-    if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns)) {
-        set_status(g.status, TM_ERR_TIMEOUT);
-    } else {
+    for (int e = 0; e < NG; ++e, ++k) {
+        const int s = k % S_IN;
+        if (k >= S_IN && !mbar_wait_bounded(&empty[s], ((k / S_IN) & 1) ^ 1, g.wait_ns)) {
+            set_status(g.status, TM_ERR_TIMEOUT);
+            return;
+        }
         StageHeader* h = reinterpret_cast<StageHeader*>(smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes);
         h->end = 1;
         mbar_arrive_expect_tx(&full[s], 0);
@@ -500,7 +505,7 @@ __device__ __forceinline__ void stage_end(const EngineArgs& g, uint8_t* smem, ui
 // Producer warp: pulls tile records from the work queue and stages them.
 // A grab of G consecutive records is packed greedily into tiles of at most
 // `cap` elements (consecutive records are adjacent on the merge path).
-template <typename K, typename V, int LOG_T, int S_IN, int SPLIT>
+template <typename K, typename V, int LOG_T, int S_IN, int SPLIT, int NG = 1>
 __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                 uint64_t* empty, int lane) {
     int k = 0;                                        // fills issued
@@ -539,7 +544,7 @@ __device__ __forceinline__ void engine_producer(const EngineArgs& g, uint8_t* sm
         base = nbase;
         d = nd;
     }
-    if (ok) stage_end<S_IN>(g, smem, full, empty, lane, k);
+    if (ok) stage_end<S_IN, NG>(g, smem, full, empty, lane, k);
 }
 
 // Fused single merge, Steps 3-4 selection done by each CTA for itself: the
@@ -611,7 +616,7 @@ __device__ __forceinline__ void fused_records(const EngineArgs& g, int64_t ca, i
 // in merge-path order and packs chain-adjacent ones (consecutive chain
 // indices: contiguous in A, B and C) into tiles of at most `cap` elements.
 // Lanes hold up to 32 records of each side at a time.
-template <typename K, typename V, int LOG_T, int S_IN, int SPLIT>
+template <typename K, typename V, int LOG_T, int S_IN, int SPLIT, int NG = 1>
 __device__ __forceinline__ void engine_producer_static(const EngineArgs& g, uint8_t* smem, uint64_t* full,
                                                        uint64_t* empty, int lane) {
     const int64_t p = g.fp, G = gridDim.x, c = blockIdx.x;
@@ -659,7 +664,7 @@ __device__ __forceinline__ void engine_producer_static(const EngineArgs& g, uint
         ta0 = a0; tb0 = b0; tA = nA; tB = nB; tnext = chain + 1;
     }
     if (ok) ok = stage_tile<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, lane, k, ta0, tb0, ta0 + tb0, tA, tB);
-    if (ok) stage_end<S_IN>(g, smem, full, empty, lane, k);
+    if (ok) stage_end<S_IN, NG>(g, smem, full, empty, lane, k);
 }
 
 // Prefetch into L2 of this CTA's share (1/parts, 16-byte granules, inside the
@@ -756,22 +761,27 @@ __device__ __forceinline__ void engine_consumers_blocks(const EngineArgs& g, uin
 
 // Consumers, equal output runs of VT elements per thread, results written
 // back into the consumed stage.  The stage is released one tile later, once
-// its bulk store has read it.
-template <typename K, typename V, int LOG_T, int S_IN, int VT, bool VALS>
+// its bulk store has read it.  NG groups of T threads take the fills in
+// turn (group j: fills j, j + NG, ...), each with its own named barrier, so
+// that NG tiles of a CTA are merged at once; with S_IN = 2 NG every group
+// owns its own pair of stages.
+template <typename K, typename V, int LOG_T, int S_IN, int VT, bool VALS, int NG = 1>
 __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, uint8_t* smem, uint64_t* full,
-                                                          uint64_t* empty, int tid) {
+                                                          uint64_t* empty, int ctid) {
     constexpr int T = 1 << LOG_T;
+    static_assert(NG == 1 || S_IN == 2 * NG, "a group needs two stages of its own");
+    const int grp = ctid >> LOG_T, tid = ctid & (T - 1), bar = 1 + grp;
     const bool leader = (tid == 0);
     int pending = -1;                                  // stage whose store is still reading it
-    int k = 0;
-    for (;; ++k) {
+    int k = grp;
+    for (;; k += NG) {
         const int s = k % S_IN;
         uint8_t* st = smem + g.lay.stages_off + (uint32_t)s * g.lay.stage_bytes;
         if (!mbar_wait_bounded(&full[s], (k / S_IN) & 1, g.wait_ns)) {
             if (leader) set_status(g.status, TM_ERR_TIMEOUT);
             break;
         }
-        if (k == 0 && leader && g.trace != nullptr)
+        if (k == 0 && leader && g.trace != nullptr)       // group 0's first tile
             g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 6] = global_timer_ns();
         const StageHeader* h = reinterpret_cast<const StageHeader*>(st);
         if (h->end) break;
@@ -815,7 +825,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
                 }
             }
         }
-        consumer_sync(T);                              // all reads of the stage's input done
+        consumer_sync(T, bar);                              // all reads of the stage's input done
         const uintptr_t gk = reinterpret_cast<uintptr_t>(g.C) + (uintptr_t)c0 * sizeof(K);
         const uintptr_t gv = reinterpret_cast<uintptr_t>(g.Cv) + (uintptr_t)c0 * sizeof(V);
         uint8_t* bk = st + g.lay.keys_off;
@@ -830,7 +840,7 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
             }
         }
         fence_proxy_async_smem();
-        consumer_sync(T);
+        consumer_sync(T, bar);
         store_out<K>(bk, g.C, c0, L, tid, T, leader);
         if constexpr (vals) store_out<V>(bv, g.Cv, c0, L, tid, T, leader);
         if (leader) {
@@ -843,13 +853,14 @@ __device__ __forceinline__ void engine_consumers_diagonal(const EngineArgs& g, u
         }
     }
     if (leader) bulk_wait_read<0>();
-    if (leader && g.trace != nullptr) g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 7] = (uint64_t)k;
+    if (leader && grp == 0 && g.trace != nullptr)        // fills taken by the CTA (the end markers excluded)
+        g.trace[(size_t)kTraceSlots * (blockIdx.x + 1) + 7] = (uint64_t)(k - grp);
 }
 
-template <typename K, typename V, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT, bool FUSED = false>
-__global__ void __launch_bounds__((1 << LOG_T) + 32)
+template <typename K, typename V, int LOG_T, int S_IN, int S_OUT, int SPLIT, int VT, bool FUSED = false, int NG = 1>
+__global__ void __launch_bounds__((1 << LOG_T) * NG + 32)
 merge_engine_kernel(const EngineArgs g) {
-    constexpr int T = 1 << LOG_T;
+    constexpr int T = (1 << LOG_T) * NG;              // consumer threads (NG groups), then the producer warp
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + g.lay.bars_off);
     uint64_t* empty = full + S_IN;
@@ -880,15 +891,20 @@ merge_engine_kernel(const EngineArgs g) {
         trace_stamp(g, 2);
     }
     if (tid >= T) {                                   // Steps 3-4: selection by the producer, then merges
-        if constexpr (FUSED) engine_producer_static<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
-        else                 engine_producer<K, V, LOG_T, S_IN, SPLIT>(g, smem, full, empty, tid - T);
+        if constexpr (FUSED) engine_producer_static<K, V, LOG_T, S_IN, SPLIT, NG>(g, smem, full, empty, tid - T);
+        else                 engine_producer<K, V, LOG_T, S_IN, SPLIT, NG>(g, smem, full, empty, tid - T);
         return;
     }
     if constexpr (SPLIT == kSplitDiagonal) {           // payloads or keys only: one branch per launch
-        if (g.Cv != nullptr) engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, true>(g, smem, full, empty, tid);
-        else                 engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, false>(g, smem, full, empty, tid);
+        if (g.Cv != nullptr) engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, true, NG>(g, smem, full, empty, tid);
+        else                 engine_consumers_diagonal<K, V, LOG_T, S_IN, VT, false, NG>(g, smem, full, empty, tid);
+    } else {
+        static_assert(SPLIT == kSplitDiagonal || NG == 1, "one consumer group with the paper's in-CTA rule");
+        engine_consumers_blocks<K, V, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
     }
-    else engine_consumers_blocks<K, V, LOG_T, S_IN, S_OUT>(g, smem, full, empty, tid);
+    if constexpr (NG > 1) {
+        if (g.trace != nullptr) consumer_sync(T, 15);  // the end stamp after every group's last tile
+    }
     trace_stamp(g, 5);
 }
 
