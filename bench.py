@@ -432,6 +432,17 @@ def guarded(fn, *args, **kwargs):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+
+def side_stream(dev):
+    """A new stream whose work starts after everything already issued on the
+    current stream.  The inputs are generated there; without the wait, a
+    kernel on the new stream can read them half written, or overwrite a
+    block the caching allocator has just handed back while a kernel on the
+    current stream still reads it."""
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    return s
+
 def bench_small_merge(dev, steps: int = 200):
     """The 1M merge: A n = 2**20, B m = 2**19 u32 keys in [0, 2**16), p = 1024
     blocks per input; one tm_merge captured in a CUDA graph and replayed (a
@@ -444,7 +455,7 @@ def bench_small_merge(dev, steps: int = 200):
     C = torch.empty(n + m, dtype=torch.int32, device=dev)
     Cv = torch.empty(n + m, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    s = torch.cuda.Stream(dev)
+    s = side_stream(dev)
     out = {"workload": "A 2^20 + B 2^19 u32 keys in [0, 2^16), u32 payloads, p = 1024; one CUDA graph replay "
                        "per merge", "elements": n + m, "unit": UNIT, "l2": "flushed before every replay"}
     ref = None
@@ -607,7 +618,7 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
     Cv = torch.empty(total, dtype=torch.int32, device=dev)
     big = max(tm.tm_merge_batched_workspace_size(pairs, ta, tb, {"tile": t}) for t in (1024, 2048, 4096))
     ws = tm.new_workspace(big, dev)
-    s = torch.cuda.Stream(dev)
+    s = side_stream(dev)
     best = cfg or tm.tm_autotune_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, stream=s)
     tm.tm_merge_batched("u64", a_off, A, Av, b_off, B, Bv, C, Cv, ws, cfg=best, stream=s)
     s.synchronize()
@@ -669,7 +680,7 @@ def bench_sort(dev, steps: int = 3, cfg=None):
     tk, tv = torch.empty_like(src_k), torch.empty_like(src_v)
     big = max(tm.tm_merge_sort_workspace_size(n, {"tile": t}) for t in (1024, 2048, 4096))
     ws = tm.new_workspace(big, dev)
-    s = torch.cuda.Stream(dev)
+    s = side_stream(dev)
     best = cfg or tm.tm_autotune_sort("u64", src_k, src_v, keys, vals, tk, tv, ws, stream=s)
     times = []
     for _ in range(steps + 1):
@@ -796,7 +807,7 @@ def bench_learned(dev, merges: int = 256, log2_base: int = 28, log2_batch: int =
     ybar = torch.empty(p_max + 1, dtype=torch.int64, device=dev)
     tiles = torch.empty(2 * p_max * tm.tm_tile_record_bytes(), dtype=torch.uint8, device=dev)
     control = torch.zeros(256, dtype=torch.uint8, device=dev)
-    s = torch.cuda.Stream(dev)
+    s = side_stream(dev)
 
     def run(search):
         bufs[0][0][:N0].copy_(X0)
@@ -1135,7 +1146,7 @@ def main():
         Cs = [(C, Cv), (torch.empty(cmax, dtype=torch.int32, device=dev), torch.empty(cmax, dtype=torch.int32, device=dev))]
         wss = [tm.new_workspace(max(tm.tm_merge_workspace_size(it["n"], it["m"], cfg) for it in items), dev)
                for _ in range(2)]
-        s_in, s_comp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        s_in, s_comp, s_out = side_stream(dev), side_stream(dev), side_stream(dev)
         h2d = d2h = 0
         out_done = [None, None]
         merged = {}                       # per merge: its last tm_merge, which read the device inputs

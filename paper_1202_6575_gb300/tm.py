@@ -5,10 +5,18 @@ and contiguity, turns tensors into device pointers and the current torch
 stream into a cudaStream_t, and calls the C entry point of the same name.
 All computation runs in the library's CUDA kernels.  There is no CPU path:
 if libtm.so is missing or no CUDA device is present, calls raise.
+
+A call given `stream` allocates (and zero-fills) the tensors it makes itself
+-- outputs, temporaries, workspaces -- on that stream, so that the caching
+allocator orders their reuse after the call's kernels.  Inputs are the
+caller's: work on another stream that produced them must be ordered before
+the call (stream.wait_stream), as for any torch operation.
 """
 from __future__ import annotations
 
 import ctypes
+import functools
+import inspect
 import os
 
 import numpy as np
@@ -167,6 +175,22 @@ def _cfg(cfg):
     return ctypes.byref(c)
 
 
+
+def _on_stream(fn):
+    """Runs the binding with `stream` (keyword or positional) as the current
+    torch stream, so that what it allocates belongs to that stream."""
+    params = list(inspect.signature(fn).parameters)
+    pos = params.index("stream")
+
+    @functools.wraps(fn)
+    def wrapped(*a, **k):
+        s = k.get("stream", a[pos] if len(a) > pos else None)
+        if s is None:
+            return fn(*a, **k)
+        with torch.cuda.stream(s):
+            return fn(*a, **k)
+    return wrapped
+
 def _stream(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -237,6 +261,7 @@ def new_workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+@_on_stream
 def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, stream=None):
     """Stable merge of (A, Av) and (B, Bv); returns (C, Cv, workspace).
     Av = Bv = None merges keys only (Cv None).  The status word is the first
@@ -261,6 +286,7 @@ def tm_merge(kt: str, A, Av, B, Bv, C=None, Cv=None, workspace=None, cfg=None, s
     return C, Cv, workspace
 
 
+@_on_stream
 def tm_cross_ranks(kt: str, A, B, p: int, xbar=None, ybar=None, stream=None):
     """Steps 1-2: returns (xbar, ybar), int64 tensors of p + 1 entries."""
     kd = TORCH_KEY_DTYPES[kt]
@@ -287,6 +313,7 @@ def tm_plan_tile_count(n: int, m: int, p: int) -> int:
     return int(load().tm_plan_tile_count(n, m, p))
 
 
+@_on_stream
 def tm_plan_subproblems(n: int, m: int, p: int, xbar, ybar, tiles=None, cfg=None, stream=None):
     """Steps 3-4 selection: tile records in merge-path order (uint8 tensor of
     room for 2p records; the first tm_plan_tile_count(n, m, p) are valid)."""
@@ -298,6 +325,7 @@ def tm_plan_subproblems(n: int, m: int, p: int, xbar, ybar, tiles=None, cfg=None
     return tiles
 
 
+@_on_stream
 def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None, Cv=None, control=None,
                    cfg=None, stream=None):
     """Steps 3-4 merges of planned tiles; returns (C, Cv, control).  The
@@ -319,6 +347,7 @@ def tm_merge_tiles(kt: str, A, Av, B, Bv, tiles, n_tiles: int, cap: int, C=None,
     return C, Cv, control
 
 
+@_on_stream
 def tm_rank_search(kt: str, kind: str, q, X, out=None, stream=None):
     """out[k] = rank_low(q[k], X) (kind 'low') or rank_high(q[k], X) ('high')."""
     kd = TORCH_KEY_DTYPES[kt]
@@ -331,6 +360,7 @@ def tm_rank_search(kt: str, kind: str, q, X, out=None, stream=None):
     return out
 
 
+@_on_stream
 def tm_subproblems(n: int, m: int, p: int, xbar, ybar, table=None, stream=None):
     """Device-computed subproblem table, int64 (2p, 4): a0, a1, b0, b1."""
     if table is None:
@@ -405,6 +435,7 @@ def _batched_args(kt, a_off, A, Av, b_off, B, Bv, C, Cv):
     return args, C, Cv, pairs, ta, tb
 
 
+@_on_stream
 def tm_merge_batched(kt: str, a_off, A, Av, b_off, B, Bv, C=None, Cv=None, workspace=None, cfg=None,
                      stream=None):
     """Independent stable merges of CSR pairs; returns (C, Cv, workspace)."""
@@ -422,6 +453,7 @@ def tm_merge_sort_workspace_size(n: int, cfg=None) -> int:
     return int(load().tm_merge_sort_workspace_size(n, _cfg(cfg)))
 
 
+@_on_stream
 def tm_merge_sort(kt: str, keys, vals, tmp_keys=None, tmp_vals=None, workspace=None, cfg=None, stream=None):
     """Stable sort of (keys, vals) in place; returns (keys, vals, workspace)."""
     kd = TORCH_KEY_DTYPES[kt]
@@ -456,6 +488,7 @@ def tm_merge_sort_segmented_workspace_size(n: int, seg_offsets, cfg=None) -> int
                                                              len(off) - 1, _cfg(cfg)))
 
 
+@_on_stream
 def tm_merge_sort_segmented(kt: str, keys, vals, seg_offsets, tmp_keys=None, tmp_vals=None, workspace=None,
                             cfg=None, stream=None):
     """Stable sort of every segment [seg_offsets[q], seg_offsets[q+1]) of
@@ -588,6 +621,7 @@ class CdfModel:
     def _p(self):
         return _dev(self.buf, "model")
 
+    @_on_stream
     def init(self, base, init_params, stream=None):
         ip = init_params.to(device=self.buf.device, dtype=torch.float32).contiguous()
         _check(load().tm_cdf_init(self._p(), self.S, self.H, _dev(base, "base", (torch.float32,)), base.numel(),
@@ -595,6 +629,7 @@ class CdfModel:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         return self
 
+    @_on_stream
     def grad(self, q, labels, stream=None):
         g = torch.empty(self.P, dtype=torch.float32, device=self.buf.device)
         loss = torch.empty(1, dtype=torch.float32, device=self.buf.device)
@@ -603,17 +638,20 @@ class CdfModel:
                                   _stream(stream)), "tm_cdf_grad")
         return g, loss
 
+    @_on_stream
     def train(self, q, labels, steps: int, lr: float, stream=None):
         _check(load().tm_cdf_train(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)),
                                    _dev(labels, "labels", (torch.int64,)), q.numel(), int(steps), float(lr),
                                    _stream(stream)), "tm_cdf_train")
 
+    @_on_stream
     def predict(self, q, stream=None):
         out = torch.empty(q.numel(), dtype=torch.float32, device=q.device)
         _check(load().tm_cdf_predict(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)), q.numel(),
                                      _dev(out, "pred"), _stream(stream)), "tm_cdf_predict")
         return out
 
+    @_on_stream
     def calibrate(self, q, labels, stream=None):
         _check(load().tm_cdf_calibrate(self._p(), self.S, self.H, _dev(q, "q", (torch.float32,)),
                                        _dev(labels, "labels", (torch.int64,)), q.numel(), _stream(stream)),
@@ -644,6 +682,7 @@ class CdfModel:
                 for name, dt, off in self.HEADER}
 
 
+@_on_stream
 def tm_cross_ranks_learned(model: CdfModel, A, B, p: int, xbar=None, ybar=None, flags: int = 0, stream=None):
     if xbar is None:
         xbar = torch.empty(p + 1, dtype=torch.int64, device=A.device)

@@ -301,3 +301,41 @@ def test_segmented_sort_offsets_and_sizing_on_the_host(lib):
     s2 = lib.tm_merge_sort_segmented_workspace_size(1 << 20, p2, 3, None)
     assert 0 < s1 < s2
     assert tm.tm_merge_sort_segmented_workspace_size(5000, [0, 1000, 1000, 5000]) == s1
+
+
+def test_binding_runs_a_call_with_its_stream_current(monkeypatch):
+    """A binding given `stream` (keyword or positional) runs with that
+    stream current, so that the tensors it allocates belong to it; without
+    one it runs on the caller's current stream."""
+    entered = []
+
+    class Ctx:
+        def __init__(self, s):
+            self.s = s
+
+        def __enter__(self):
+            entered.append(self.s)
+
+        def __exit__(self, *exc):
+            return False
+
+    monkeypatch.setattr(tm.torch.cuda, "stream", Ctx)
+
+    @tm._on_stream
+    def call(a, b=None, stream=None):
+        return (a, b, stream, list(entered))
+
+    assert call(1) == (1, None, None, [])
+    assert call(1, 2, stream="S1") == (1, 2, "S1", ["S1"])
+    assert call(1, 2, "S2") == (1, 2, "S2", ["S1", "S2"])
+    assert call(1, stream=None)[3] == ["S1", "S2"]
+
+    class M:
+        @tm._on_stream
+        def meth(self, q, stream=None):
+            return stream
+
+    assert M().meth(3, "S3") == "S3" and entered[-1] == "S3"
+    for f in (tm.tm_merge, tm.tm_merge_sort, tm.tm_merge_batched, tm.tm_merge_tiles, tm.tm_cross_ranks,
+              tm.tm_merge_sort_segmented, tm.tm_cross_ranks_learned, tm.CdfModel.train):
+        assert getattr(f, "__wrapped__", None) is not None, f.__name__

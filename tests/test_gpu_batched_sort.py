@@ -240,3 +240,25 @@ def test_merge_sort_full_size():
     OK, OV = oracle.merge_sort(src_k, src_v, run=32)
     assert first_mismatch(ck, OK) is None
     assert first_mismatch(cv, OV) is None
+
+
+def test_merge_sort_on_a_side_stream_with_binding_temporaries():
+    """A call given a stream other than the current one makes its
+    temporaries (tmp_keys, tmp_vals, workspace) on that stream: allocations
+    of the same sizes on the current stream, filled at once while the sort
+    still runs, cannot take their blocks."""
+    n = 1 << 24
+    g = torch.Generator().manual_seed(5)
+    keys = torch.randint(0, 1 << 16, (n,), generator=g, dtype=torch.int64)
+    vals = torch.arange(n, dtype=torch.int32)
+    k, v = keys.to(DEV), vals.to(DEV)
+    s = torch.cuda.Stream(DEV)
+    s.wait_stream(torch.cuda.current_stream(DEV))
+    K, V, ws = tm.tm_merge_sort("u64", k, v, stream=s)
+    junk = [torch.full((n,), -1, dtype=torch.int64, device=DEV), torch.full((n,), -1, dtype=torch.int32, device=DEV)]
+    torch.cuda.synchronize()
+    assert tm.tm_read_status(ws) == 0
+    OK, OV = oracle.merge_sort(to_np(keys, "u64"), vals_np(vals), run=32)
+    assert first_mismatch(to_np(K, "u64"), OK) is None
+    assert first_mismatch(vals_np(V), OV) is None
+    del junk
