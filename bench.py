@@ -433,6 +433,10 @@ def guarded(fn, *args, **kwargs):
 
 
 
+# Elements per initial sorted run of tm_merge_sort (one CTA's radix sort);
+# the merge rounds double it.
+SORT_RUN = 4096
+
 def side_stream(dev):
     """A new stream whose work starts after everything already issued on the
     current stream.  The inputs are generated there; without the wait, a
@@ -672,7 +676,7 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
 
 def bench_sort(dev, steps: int = 3, cfg=None):
     """Stable merge sort of 2**28 u64 keys uniform in [0, 2**24) with u32
-    payloads (original index): sorted runs of 1024, then 18 merge rounds."""
+    payloads (original index): sorted runs of 4096, then 16 merge rounds."""
     from paper_1202_6575_gb300 import tm, workloads as W
     src_k, src_v = W.sort_input(dev)
     n = src_k.numel()
@@ -721,7 +725,7 @@ def bench_sort(dev, steps: int = 3, cfg=None):
     del k0, k1, v0, v1, idx
     ums = float(np.median(utimes[1:]))
     rounds = 0
-    r = 1024
+    r = SORT_RUN
     while r < n:
         r *= 2
         rounds += 1
@@ -776,7 +780,7 @@ def bench_segmented(dev, steps: int = 3):
     s0, s1, k0, k1, v0, v1 = seg[:-1], seg[1:], keys[:-1], keys[1:], vals[:-1], vals[1:]
     ok = ok and bool(((s0 != s1) | (k0 < k1) | ((k0 == k1) & (v0 < v1))).all())
     rounds = 0
-    while (1024 << rounds) < int(lens.max()):
+    while (SORT_RUN << rounds) < int(lens.max()):
         rounds += 1
     moved = n * 24 * (rounds + 1)
     gbs = moved / (ms / 1e3) / 1e9

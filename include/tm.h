@@ -298,11 +298,12 @@ TM_API tm_status tm_merge_batched(tm_key_type kt, int64_t num_pairs,
 /* Workspace bytes of tm_merge_sort for n elements. */
 TM_API size_t tm_merge_sort_workspace_size(int64_t n, const tm_config* cfg);
 
-/* Stable sort of (keys, vals) by key (Section 3): consecutive runs of 1024
- * elements are sorted inside one CTA each (every element placed by the
- * position formulas of Section 2 over doubling sub-runs), then ceil(log2(n /
- * 1024)) rounds merge adjacent runs pairwise (an unpaired last run is
- * copied), every round one batched merge of uniform pairs.  With
+/* Stable sort of (keys, vals) by key (Section 3): consecutive runs of 4096
+ * elements are sorted inside one CTA each (a stable LSD radix sort of the
+ * keys' order-preserving images, 8 bits per pass, skipping the bytes in
+ * which all keys of the run agree), then ceil(log2(n / 4096)) rounds merge
+ * adjacent runs pairwise (an unpaired last run is copied), every round one
+ * batched merge of uniform pairs.  With
  * cfg->merge_ways = 4, two consecutive rounds are done in one pass over
  * memory: groups of four runs R0..R3 become merge(merge(R0, R1), merge(R2,
  * R3)), the subproblems chosen by the paper's method on the outer merge of
@@ -319,7 +320,7 @@ TM_API tm_status tm_merge_sort(tm_key_type kt, void* keys, uint32_t* vals, int64
 /* Segmented stable sort: num_segments independent segments of one array,
  * segment q = (keys, vals)[seg_offsets[q], seg_offsets[q+1]), each sorted
  * stably by key (Section 3's merge sort inside every segment: runs of at
- * most 1024 elements that never cross a segment boundary, then rounds that
+ * most 4096 elements that never cross a segment boundary, then rounds that
  * merge each segment's neighbouring runs pairwise, one batched merge per
  * round; a segment already sorted is copied).  seg_offsets is HOST memory
  * (num_segments + 1 int64, from 0, non-decreasing, ending at n): the host

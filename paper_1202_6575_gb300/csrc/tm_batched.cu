@@ -19,6 +19,7 @@
 #include "tm_engine.cuh"
 #include "tm_engine4.cuh"
 #include "tm_host.h"
+#include "tm_runsort.cuh"
 
 namespace pmerge {
 
@@ -457,127 +458,17 @@ static tm_status batched_typed(int64_t pairs, const int64_t* a_off, const void* 
 // Stable merge sort (Section 3): stable sorted runs, then merge rounds
 // ---------------------------------------------------------------------------
 
-// Stable in-CTA sort of consecutive runs of 1024 elements (Section 3's
-// "sort p consecutive blocks sequentially", done by one CTA per block):
-// 128 threads hold 9 consecutive elements each in registers and sort them
-// with an odd-even transposition network that exchanges only on a strict
-// '>' (stable); then 7 merge levels double the sorted run length from 9 to
-// 1152 >= 1024.  At each level thread t owns 9 consecutive outputs of its
-// pair of runs: it finds where its output diagonal crosses the two runs with
-// the co-rank condition of the position formulas (Section 2: i elements of
-// the left run precede output d iff R[d-i-1] < L[i] and L[i-1] <= R[d-i])
-// and merges its 9 outputs serially, taking the right run only on a
-// strictly smaller key.  Runs live in shared memory between levels; the odd
-// count per thread keeps the register <-> shared exchanges free of bank
-// conflicts (lanes 9 words apart).
-constexpr int kSortRun = 1024;
-constexpr int kSortThreads = 128;
-constexpr int kSortVT = 9;
-
-// rdesc (optional): run b is X[rdesc[2b], rdesc[2b] + rdesc[2b+1]) (at most
-// kSortRun elements); without it run b is X[b kSortRun, ...) clipped to n.
+// The stable sorted runs (tm_runsort.cuh): one CTA per run, its keys,
+// payloads and digit counts in dynamic shared memory.
 template <typename K, typename V>
-__global__ void __launch_bounds__(kSortThreads)
-run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __restrict__ out_k,
-                V* __restrict__ out_v, int64_t n, const int64_t* __restrict__ rdesc = nullptr) {
-    __shared__ K sk[kSortRun + 1];                    // + 1: the merge step reads one past a run
-    __shared__ V sv[kSortRun];
-    const int t = threadIdx.x;
-    const int64_t base = rdesc ? __ldg(rdesc + 2 * blockIdx.x) : (int64_t)blockIdx.x * kSortRun;
-    const int64_t rl = rdesc ? __ldg(rdesc + 2 * blockIdx.x + 1) : n - base;
-    const int len = (int)(rl < kSortRun ? (rl > 0 ? rl : 0) : kSortRun);
-    for (int i = t; i < len; i += kSortThreads) {      // no payloads (keys-only sort): sv unused
-        sk[i] = in_k[base + i];
-        if (in_v) sv[i] = in_v[base + i];
-    }
-    __syncthreads();
-    // blocked registers: thread t holds elements [kSortVT*t, kSortVT*(t+1)); missing ones
-    // (past len) are marked invalid and sort to the end
-    K k[kSortVT];
-    V v[kSortVT];
-    bool ok[kSortVT];
-#pragma unroll
-    for (int q = 0; q < kSortVT; ++q) {
-        const int i = t * kSortVT + q;
-        ok[q] = i < len;
-        k[q] = K();
-        v[q] = V();
-        if (ok[q]) { k[q] = sk[i]; v[q] = sv[i]; }
-    }
-    // stable odd-even transposition sort of kSortVT (invalid elements are largest)
-#pragma unroll
-    for (int r = 0; r < kSortVT; ++r) {
-#pragma unroll
-        for (int q = r & 1; q + 1 < kSortVT; q += 2) {
-            const bool swap = ok[q + 1] && (!ok[q] || k[q + 1] < k[q]);
-            if (swap) {
-                const K tk = k[q]; k[q] = k[q + 1]; k[q + 1] = tk;
-                const V tv = v[q]; v[q] = v[q + 1]; v[q + 1] = tv;
-                const bool to = ok[q]; ok[q] = ok[q + 1]; ok[q + 1] = to;
-            }
-        }
-    }
-    for (int w = kSortVT; w < kSortRun; w <<= 1) {
-        // a pair of runs of 2w <= 32 * kSortVT elements lies inside one warp's
-        // 288 outputs: those levels synchronise the warp only
-        const bool in_warp = 2 * w <= 32 * kSortVT;
-        if (in_warp) __syncwarp(); else __syncthreads();  // previous level's reads are done
-#pragma unroll
-        for (int q = 0; q < kSortVT; ++q) {
-            const int i = t * kSortVT + q;
-            if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
-        }
-        if (in_warp) __syncwarp(); else __syncthreads();
-        const int d0 = t * kSortVT;                       // first output this thread owns
-        const int lo = (d0 / (2 * w)) * (2 * w);          // start of its pair of runs (w = 9 * 2^k)
-        const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
-        const int nl = mid - lo, nr = hi - mid;
-        const int d = d0 - lo;                            // diagonal inside the pair
-        int cnt = min(kSortVT, hi - d0);
-        if (cnt < 0) cnt = 0;
-        const K* L = sk + lo;
-        const K* Rr = sk + mid;
-        int i = 0, j = 0;
-        if (cnt > 0) {
-            int a = d > nr ? d - nr : 0, b = d < nl ? d : nl;
-            while (a < b) {
-                const int m2 = (a + b) >> 1;
-                if (Rr[d - m2 - 1] < L[m2]) b = m2; else a = m2 + 1;
-            }
-            i = a;
-            j = d - a;
-        }
-        K kl = (i < nl) ? L[i] : K(), kr = (j < nr) ? Rr[j] : K();
-#pragma unroll
-        for (int q = 0; q < kSortVT; ++q) {
-            ok[q] = q < cnt;
-            if (q < cnt) {                                // branch-free: select, then one load each
-                const bool takeR = (j < nr) && ((i >= nl) || (kr < kl));
-                const int src = takeR ? mid + j : lo + i;
-                k[q] = takeR ? kr : kl;
-                v[q] = sv[src];
-                const K nk = sk[src + 1];                 // past a run's end: never selected
-                kr = takeR ? nk : kr;
-                kl = takeR ? kl : nk;
-                j += takeR ? 1 : 0;
-                i += takeR ? 0 : 1;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kSortVT; ++q) {
-        const int i = t * kSortVT + q;
-        if (i < len) { sk[i] = k[q]; sv[i] = v[q]; }
-    }
-    __syncthreads();
-    for (int i = t; i < len; i += kSortThreads) {
-        out_k[base + i] = sk[i];
-        if (out_v) out_v[base + i] = sv[i];
-    }
+static tm_status launch_run_sort(unsigned runs, const K* in_k, const V* in_v, K* out_k, V* out_v, int64_t n,
+                                 const int64_t* rdesc, cudaStream_t s) {
+    if (runs == 0) return TM_OK;
+    constexpr uint32_t smem = run_sort_smem_bytes<K, V>();
+    if (!ensure_smem_limit(run_sort_kernel<K, V>, smem)) return TM_ERR_UNSUPPORTED;
+    run_sort_kernel<K, V><<<runs, kSortThreads, smem, s>>>(in_k, in_v, out_k, out_v, n, rdesc);
+    return launch_status();
 }
-
-
 
 // Pair set of the merge round with sorted runs of length `run`.
 static PairSet sort_round(int64_t n, int64_t run, int64_t tile, int64_t* items) {
@@ -804,7 +695,7 @@ static tm_status sort_typed_v(void* keys, void* vals, int64_t n, void* tmp_keys,
     if (n <= 1) return TM_OK;
     K* bufk[2] = {static_cast<K*>(keys), static_cast<K*>(tmp_keys)};
     V* bufv[2] = {static_cast<V*>(vals), static_cast<V*>(tmp_vals)};
-    // pairwise rounds (run 1024, 2048, ...), fused two at a time when the
+    // pairwise rounds (run 4096, 8192, ...), fused two at a time when the
     // configuration allows; the number of passes decides where the run
     // formation writes, so that the last pass lands in (keys, vals)
     int rounds = 0;
@@ -817,8 +708,8 @@ static tm_status sort_typed_v(void* keys, void* vals, int64_t n, void* tmp_keys,
     int src = (passes % 2 == 0) ? 0 : 1;
     const int64_t runs = (n + kSortRun - 1) / kSortRun;
     if (runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
-    run_sort_kernel<K, V><<<(unsigned)runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n);
-    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
+    if (const tm_status st_ = launch_run_sort<K, V>((unsigned)runs, bufk[0], bufv[0], bufk[src], bufv[src], n,
+                                                     nullptr, s); st_ != TM_OK) return st_;
     int64_t run = kSortRun;
     for (int f = 0; f < fused; ++f, run *= 4) {
         const int dst = src ^ 1;
@@ -849,11 +740,11 @@ static tm_status sort_typed(void* keys, uint32_t* vals, int64_t n, void* tmp_key
 // ---------------------------------------------------------------------------
 // Segmented stable merge sort: independent segments of one array
 // ---------------------------------------------------------------------------
-// Runs of at most 1024 elements inside each segment (a run never crosses a
-// segment boundary), then rounds of width w = 1024, 2048, ...: in every
-// round each segment's neighbouring runs are merged pairwise (a last
-// unpaired run, or a segment already sorted, is a pair with an empty second
-// run: a copy).  The plan is made on the host from the host's segment
+// Runs of at most kSortRun elements inside each segment (a run never
+// crosses a segment boundary), then rounds of width w = kSortRun,
+// 2 kSortRun, ...: in every round each segment's neighbouring runs are
+// merged pairwise (a last unpaired run, or a segment already sorted, is a
+// pair with an empty second run: a copy).  The plan is made on the host from the host's segment
 // offsets; every round is one batched merge over explicit pairs.
 
 struct SegPlan {
@@ -968,8 +859,8 @@ static tm_status sort_segmented_v(void* keys, void* vals, int64_t n, void* tmp_k
     const int rounds = (int)P.round_pairs.size();
     int src = (rounds % 2 == 0) ? 0 : 1;
     if (P.runs > 0x7fffffffLL) return TM_ERR_UNSUPPORTED;
-    run_sort_kernel<K, V><<<(unsigned)P.runs, kSortThreads, 0, s>>>(bufk[0], bufv[0], bufk[src], bufv[src], n, x.rd);
-    if (const tm_status st_ = launch_status(); st_ != TM_OK) return st_;
+    if (const tm_status st_ = launch_run_sort<K, V>((unsigned)P.runs, bufk[0], bufv[0], bufk[src], bufv[src], n,
+                                                     x.rd, s); st_ != TM_OK) return st_;
     int64_t wd = kSortRun;
     for (int r = 0; r < rounds; ++r, wd *= 2) {
         seg_prefix_kernel<<<1, 1024, 0, s>>>(x.off, P.segs, 2 * wd, x.pre);

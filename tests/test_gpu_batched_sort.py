@@ -162,7 +162,7 @@ def sort_check(keys, vals, kt, cfg=None):
     assert first_mismatch(vals_np(V), OV) is None, "payloads"
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 1000, 1024, 1025, 2048, 5000, 65537, (1 << 20) + 3])
+@pytest.mark.parametrize("n", [0, 1, 2, 1000, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3])
 @pytest.mark.parametrize("kt", ["u64", "u32"])
 def test_merge_sort_sizes(n, kt):
     g = torch.Generator().manual_seed(n)
@@ -192,8 +192,8 @@ def test_merge_sort_configs(split):
         sort_check(keys, vals, "u64", cfg={"tile": tile, "split": split})
 
 
-@pytest.mark.parametrize("n", [2049, 3 * 1024 + 5, 4096, 4097, 4 * 4096 - 1, 4 * 4096 + 1, 5 * 4096 + 3,
-                               16 * 4096 + 1000])
+@pytest.mark.parametrize("n", [2049, 3 * 4096 + 5, 16384, 16385, 4 * 16384 - 1, 4 * 16384 + 1, 5 * 16384 + 3,
+                               16 * 16384 + 1000])
 @pytest.mark.parametrize("alphabet", [1, 3, 1 << 12])
 def test_fused_sort_rounds_against_the_oracle(n, alphabet):
     """Two rounds fused into one pass (cfg merge_ways = 4: groups of four
@@ -262,3 +262,34 @@ def test_merge_sort_on_a_side_stream_with_binding_temporaries():
     assert first_mismatch(to_np(K, "u64"), OK) is None
     assert first_mismatch(vals_np(V), OV) is None
     del junk
+
+
+DIGIT_CASES = ["top_byte", "full_64", "word_edge", "all_equal", "low_and_top", "u32_top"]
+
+
+@pytest.mark.parametrize("case", DIGIT_CASES)
+def test_run_formation_digit_windows(case):
+    """The runs are sorted by 8-bit digits, skipping the bytes in which all
+    keys of a run agree: keys that differ only in the top byte, in all 64
+    bits, only in bits 31 and 32, nowhere, or in the lowest and the top byte
+    (middle passes skipped); n spans three full runs of 4096 and a partial
+    one.  The result is the oracle's stable sort."""
+    n = 3 * 4096 + 17
+    rng = np.random.default_rng(31 + DIGIT_CASES.index(case))
+    if case == "top_byte":
+        hk = rng.integers(0, 256, n, dtype=np.uint64) << np.uint64(56)
+    elif case == "full_64":
+        hk = rng.integers(0, 1 << 63, n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64)
+    elif case == "word_edge":
+        hk = (rng.integers(0, 4, n, dtype=np.uint64) << np.uint64(31)) | np.uint64(0x5555)
+    elif case == "all_equal":
+        hk = np.full(n, 0x0123456789ABCDEF, dtype=np.uint64)
+    elif case == "low_and_top":
+        hk = (rng.integers(0, 4, n, dtype=np.uint64) << np.uint64(62)) | rng.integers(0, 3, n, dtype=np.uint64)
+    else:
+        hk = (rng.integers(0, 200, n, dtype=np.uint32) << np.uint32(24)).astype(np.uint32)
+    kt = "u32" if case == "u32_top" else "u64"
+    keys = torch.from_numpy(hk.view(np.int32) if kt == "u32" else hk.view(np.int64))
+    vals = torch.arange(n, dtype=torch.int32)
+    sort_check(keys, vals, kt)
+    sort_check(keys, vals, kt, cfg={"merge_ways": 4})

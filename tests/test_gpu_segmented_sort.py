@@ -37,7 +37,7 @@ def check(keys, vals, offs, kt, cfg=None):
 
 @pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
 def test_segment_length_mix(kt):
-    lens = [0, 1, 2, 1023, 1024, 1025, 0, 2048, 5000, 3, 70000, 0, 1 << 17, 777]
+    lens = [0, 1, 2, 1023, 1024, 1025, 0, 2048, 4095, 4096, 4097, 8193, 5000, 3, 70000, 0, 1 << 17, 777]
     offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     n = int(offs[-1])
     g = torch.Generator().manual_seed(len(kt))
