@@ -84,7 +84,7 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, bool ok, bool all_ok
     for (int b = 0; b < kRadixBits; ++b) {
         const bool bit = (d >> b) & 1u;
         const unsigned v = __ballot_sync(0xffffffffu, bit);
-        m &= bit ? v : ~v;
+        m &= ~(v ^ (0u - (unsigned)bit));             // v where the bit is set, ~v where clear
     }
     return m;
 }
@@ -117,31 +117,24 @@ __device__ __forceinline__ int cta_exclusive_scan(int x, int* tot) {
     return r;
 }
 
-// rdesc (optional): run b is X[rdesc[2b], rdesc[2b] + rdesc[2b+1]) (at most
-// kSortRun elements); without it run b is X[b kSortRun, ...) clipped to n.
-// in_v == nullptr (and out_v): keys only.  The run may be sorted in place
-// (in == out).
-template <typename K, typename V>
-__global__ void __launch_bounds__(kSortThreads, 2)
-run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __restrict__ out_k,
-                V* __restrict__ out_v, int64_t n, const int64_t* __restrict__ rdesc = nullptr) {
+// One run X[base, base + len) (len <= kSortRun; FULL: len == kSortRun, so
+// that no item needs a bounds check).
+template <typename K, typename V, bool FULL>
+__device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const V* __restrict__ in_v,
+                                              K* __restrict__ out_k, V* __restrict__ out_v, int64_t base,
+                                              int len, uint8_t* smem) {
     using R = RadixImage<K>;
     using U = typename R::U;
-    extern __shared__ __align__(128) uint8_t smem[];
     K* sk = reinterpret_cast<K*>(smem);
     V* sv = reinterpret_cast<V*>(smem + (size_t)kSortRun * sizeof(K));
     int* hist = reinterpret_cast<int*>(smem + (size_t)kSortRun * (sizeof(K) + sizeof(V)));  // [warp][digit]
     __shared__ U red[kSortWarps], red2[kSortWarps];
     __shared__ int tot[kSortWarps];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t base = rdesc ? __ldg(rdesc + 2 * blockIdx.x) : (int64_t)blockIdx.x * kSortRun;
-    const int64_t rl = rdesc ? __ldg(rdesc + 2 * blockIdx.x + 1) : n - base;
-    const int len = (int)(rl < kSortRun ? (rl > 0 ? rl : 0) : kSortRun);
-    if (len == 0) return;                              // the same for the whole CTA
     const bool vals = in_v != nullptr;
-    const bool full = len == kSortRun;
     const int p0 = w * 32 * kSortVT + lane;            // item q sits at p0 + 32 q
     const uint32_t lt_mask = (1u << lane) - 1u;
+    auto has = [&](int q) { return FULL || p0 + 32 * q < len; };
 
     K k[kSortVT];
     V v[kSortVT];
@@ -150,7 +143,7 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
         const int i = p0 + 32 * q;
         k[q] = K();
         v[q] = V();
-        if (i < len) {
+        if (has(q)) {
             k[q] = in_k[base + i];
             if (vals) v[q] = in_v[base + i];
         }
@@ -159,7 +152,7 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
     U any = 0, all = ~(U)0;
 #pragma unroll
     for (int q = 0; q < kSortVT; ++q)
-        if (p0 + 32 * q < len) {
+        if (has(q)) {
             any |= R::of(k[q]);
             all &= R::of(k[q]);
         }
@@ -184,7 +177,7 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
 #pragma unroll
             for (int q = 0; q < kSortVT; ++q) {
                 const int i = p0 + 32 * q;
-                if (i < len) {
+                if (has(q)) {
                     k[q] = sk[i];
                     if (vals) v[q] = sv[i];
                 }
@@ -195,9 +188,9 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
         int dl[kSortVT];                               // digit << 16 | rank among the warp's earlier items of it
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
-            const bool ok = p0 + 32 * q < len;
+            const bool ok = has(q);
             const int d = (int)((R::of(k[q]) >> sh) & (U)(kRadixDigits - 1));
-            const unsigned peers = digit_peers((unsigned)d, ok, full);
+            const unsigned peers = digit_peers((unsigned)d, ok, FULL);
             const int leader = __ffs(peers) - 1;
             int b = 0;
             if (ok && lane == leader) b = hw[d];
@@ -227,7 +220,7 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
-            if (p0 + 32 * q < len) {
+            if (has(q)) {
                 const int dst = hw[dl[q] >> 16] + (dl[q] & 0xffff);
                 sk[dst] = k[q];
                 if (vals) sv[dst] = v[q];
@@ -245,12 +238,28 @@ run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __res
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
             const int i = p0 + 32 * q;
-            if (i < len) {
+            if (has(q)) {
                 out_k[base + i] = k[q];
                 if (vals) out_v[base + i] = v[q];
             }
         }
     }
+}
+
+// rdesc (optional): run b is X[rdesc[2b], rdesc[2b] + rdesc[2b+1]) (at most
+// kSortRun elements); without it run b is X[b kSortRun, ...) clipped to n.
+// in_v == nullptr (and out_v): keys only.  The run may be sorted in place
+// (in == out).
+template <typename K, typename V>
+__global__ void __launch_bounds__(kSortThreads, 2)
+run_sort_kernel(const K* __restrict__ in_k, const V* __restrict__ in_v, K* __restrict__ out_k,
+                V* __restrict__ out_v, int64_t n, const int64_t* __restrict__ rdesc = nullptr) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int64_t base = rdesc ? __ldg(rdesc + 2 * blockIdx.x) : (int64_t)blockIdx.x * kSortRun;
+    const int64_t rl = rdesc ? __ldg(rdesc + 2 * blockIdx.x + 1) : n - base;
+    const int len = (int)(rl < kSortRun ? (rl > 0 ? rl : 0) : kSortRun);
+    if (len == kSortRun) run_sort_body<K, V, true>(in_k, in_v, out_k, out_v, base, len, smem);
+    else if (len > 0)    run_sort_body<K, V, false>(in_k, in_v, out_k, out_v, base, len, smem);
 }
 
 }  // namespace pmerge
