@@ -20,9 +20,11 @@
 // digit bit; earlier lanes first) and keeps a running count per digit; one
 // exclusive scan of the counts in (digit, warp) order then gives every
 // digit's and warp's first output position, and each item lands at that
-// position plus its rank.  Keys and payloads move through shared memory;
-// the counts are [warp][digit], so that the per-digit updates of one warp
-// fall on distinct banks.
+// position plus its rank.  Keys move through shared memory and registers;
+// payloads only through shared memory (two buffers, each item's payload
+// copied from its old position to its new one), which keeps them out of the
+// registers during the ranking.  The counts are [warp][digit], so that the
+// per-digit updates of one warp fall on distinct banks.
 #pragma once
 #include <cstdint>
 
@@ -67,7 +69,7 @@ template <> struct RadixImage<float> {
 
 template <typename K, typename V>
 constexpr uint32_t run_sort_smem_bytes() {
-    return (uint32_t)(kSortRun * (sizeof(K) + sizeof(V)) + sizeof(int) * kRadixDigits * kSortWarps);
+    return (uint32_t)(kSortRun * (sizeof(K) + 2 * sizeof(V)) + sizeof(int) * kRadixDigits * kSortWarps);
 }
 
 // The lanes of the warp whose digit equals this lane's, among the lanes with
@@ -126,8 +128,8 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
     using R = RadixImage<K>;
     using U = typename R::U;
     K* sk = reinterpret_cast<K*>(smem);
-    V* sv = reinterpret_cast<V*>(smem + (size_t)kSortRun * sizeof(K));
-    int* hist = reinterpret_cast<int*>(smem + (size_t)kSortRun * (sizeof(K) + sizeof(V)));  // [warp][digit]
+    V* sv = reinterpret_cast<V*>(smem + (size_t)kSortRun * sizeof(K));          // payloads, two buffers
+    int* hist = reinterpret_cast<int*>(smem + (size_t)kSortRun * (sizeof(K) + 2 * sizeof(V)));  // [warp][digit]
     __shared__ U red[kSortWarps], red2[kSortWarps];
     __shared__ int tot[kSortWarps];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -137,17 +139,16 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
     auto has = [&](int q) { return FULL || p0 + 32 * q < len; };
 
     K k[kSortVT];
-    V v[kSortVT];
 #pragma unroll
     for (int q = 0; q < kSortVT; ++q) {
         const int i = p0 + 32 * q;
         k[q] = K();
-        v[q] = V();
         if (has(q)) {
             k[q] = in_k[base + i];
-            if (vals) v[q] = in_v[base + i];
+            if (vals) sv[i] = in_v[base + i];
         }
     }
+    int cur = 0;                                       // payload buffer holding the current order
     // the bits in which the run's keys differ: set in some key, clear in another
     U any = 0, all = ~(U)0;
 #pragma unroll
@@ -177,10 +178,7 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
 #pragma unroll
             for (int q = 0; q < kSortVT; ++q) {
                 const int i = p0 + 32 * q;
-                if (has(q)) {
-                    k[q] = sk[i];
-                    if (vals) v[q] = sv[i];
-                }
+                if (has(q)) k[q] = sk[i];
             }
         }
         for (int j = t; j < kRadixDigits * kSortWarps; j += kSortThreads) hist[j] = 0;
@@ -223,16 +221,17 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
             if (has(q)) {
                 const int dst = hw[dl[q] >> 16] + (dl[q] & 0xffff);
                 sk[dst] = k[q];
-                if (vals) sv[dst] = v[q];
+                if (vals) sv[(cur ^ 1) * kSortRun + dst] = sv[cur * kSortRun + p0 + 32 * q];
             }
         }
         __syncthreads();
         in_smem = true;
+        cur ^= 1;
     }
     if (in_smem) {
         for (int i = t; i < len; i += kSortThreads) {
             out_k[base + i] = sk[i];
-            if (vals) out_v[base + i] = sv[i];
+            if (vals) out_v[base + i] = sv[cur * kSortRun + i];
         }
     } else {                                           // no pass: the run was already in order
 #pragma unroll
@@ -240,7 +239,7 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
             const int i = p0 + 32 * q;
             if (has(q)) {
                 out_k[base + i] = k[q];
-                if (vals) out_v[base + i] = v[q];
+                if (vals) out_v[base + i] = sv[i];
             }
         }
     }
