@@ -25,7 +25,9 @@ superstep:
    payloads) to it; each piece is a contiguous part of one slice;
 5. every rank merges its two segments (tm_merge) into its piece of C.
 
-The result is C distributed in G contiguous pieces in rank order.  The
+The result is C distributed in G contiguous pieces in rank order.
+sort_distributed builds Section 3's merge sort on it: every rank sorts its
+slice, then rounds of this merge join neighbouring groups of ranks.  The
 collectives go through a small communicator interface: torch.distributed
 (NCCL for device tensors, gloo for host tensors) or threads of one process
 (for running the protocol of several ranks against one device).  The
@@ -87,6 +89,19 @@ class TorchComm:
         self.dist.all_to_all_single(out, t.contiguous(), recv, send, group=self.group)
         return out
 
+    def split(self, groups: list) -> "TorchComm":
+        """The communicator of this rank's group: groups partitions this
+        communicator's ranks into lists (in rank order).  Collective: every
+        process of the job calls it with the same groups."""
+        base = (list(range(self.size)) if self.group is None
+                else self.dist.get_process_group_ranks(self.group))
+        mine = None
+        for grp in groups:
+            pg = self.dist.new_group(ranks=[base[r] for r in grp])
+            if self.rank in grp:
+                mine = TorchComm(pg)
+        return mine
+
 
 class ThreadHub:
     """Shared state of G ThreadComm ranks (one Python thread each)."""
@@ -95,9 +110,27 @@ class ThreadHub:
         self.size = size
         self.barrier = threading.Barrier(size)
         self.slots = [None] * size
+        self._subs = {}
+        self._lock = threading.Lock()
 
     def comm(self, rank: int) -> "ThreadComm":
         return ThreadComm(self, rank)
+
+    def sub(self, key, size: int) -> "ThreadHub":
+        """The hub of one group of a split (made by its first rank to ask)."""
+        with self._lock:
+            h = self._subs.get(key)
+            if h is None:
+                h = self._subs[key] = ThreadHub(size)
+            return h
+
+    def abort(self):
+        """Releases every rank waiting here or in a group split from here."""
+        self.barrier.abort()
+        with self._lock:
+            subs = list(self._subs.values())
+        for h in subs:
+            h.abort()
 
 
 class ThreadComm:
@@ -106,6 +139,7 @@ class ThreadComm:
 
     def __init__(self, hub: ThreadHub, rank: int):
         self.hub, self.rank, self.size = hub, rank, hub.size
+        self._splits = 0                              # splits made so far (the same on every rank)
 
     def _exchange(self, value):
         h = self.hub
@@ -133,6 +167,14 @@ class ThreadComm:
             pieces.append(tt[o:o + ss[self.rank]])
             assert ss[self.rank] == recv[src], "send and receive counts disagree"
         return torch.cat(pieces) if pieces else t[:0]
+
+    def split(self, groups: list) -> "ThreadComm":
+        """The communicator of this rank's group (groups partitions the ranks)."""
+        self._splits += 1
+        for grp in groups:
+            if self.rank in grp:
+                return ThreadComm(self.hub.sub((self._splits, tuple(grp)), len(grp)), grp.index(self.rank))
+        raise ValueError("rank in no group")
 
 
 # ---------------------------------------------------------------------------
@@ -180,6 +222,16 @@ class GpuOps:
         if status != 0:
             raise RuntimeError(f"tm_merge: {self.tm.tm_status_str(status)}")
         return C, Cv
+
+    def sort(self, K, Kv):
+        """Stable sort of copies of (K, Kv) (tm_merge_sort)."""
+        K = K.clone()
+        Kv = None if Kv is None else Kv.clone()
+        K, Kv, ws = self.tm.tm_merge_sort(self.kt, K, Kv, cfg=self.cfg)
+        status = self.tm.tm_read_status(ws)
+        if status != 0:
+            raise RuntimeError(f"tm_merge_sort: {self.tm.tm_status_str(status)}")
+        return K, Kv
 
 
 # ---------------------------------------------------------------------------
@@ -254,3 +306,32 @@ def merge_distributed(A: torch.Tensor, Av, B: torch.Tensor, Bv, comm, ops, p: in
     C, Cv = ops.merge(SA, SAv, SB, SBv)
     plan = {"n": n, "m": m, "p": p, "bounds": bounds, "records": R}
     return C, Cv, a_lo + b_lo, plan
+
+
+def sort_distributed(K: torch.Tensor, Kv, comm, ops):
+    """Stable sort of an array distributed over the G ranks of comm: rank g
+    holds the contiguous slice (K, Kv) of it (any length, empty allowed; the
+    array is the slices in rank order; Kv = None sorts keys only).  Section
+    3's merge sort on distributed memory: every rank sorts its slice
+    (ops.sort), then ceil(log2 G) rounds of merge_distributed; in round r
+    the groups of 2^(r+1) neighbouring ranks merge the sorted arrays of their
+    two halves (left half A, right half B, so that equal keys keep their
+    global order), each group through its own communicator.  Returns (C, Cv,
+    c_lo): this rank's piece of the sorted array, which starts at global
+    index c_lo; the pieces are contiguous in rank order."""
+    G, g = comm.size, comm.rank
+    C, Cv = ops.sort(K, Kv)
+    width = 1
+    while width < G:
+        groups = [list(range(s, min(G, s + 2 * width))) for s in range(0, G, 2 * width)]
+        sub = comm.split(groups)
+        if sub.size > width:                          # the group has a right half: merge the halves
+            empty_v = None if Cv is None else Cv[:0]
+            if g % (2 * width) < width:
+                C, Cv, _, _ = merge_distributed(C, Cv, C[:0], empty_v, sub, ops)
+            else:
+                C, Cv, _, _ = merge_distributed(C[:0], empty_v, C, Cv, sub, ops)
+        width *= 2
+    lens = comm.allgather(torch.tensor([C.numel()], dtype=torch.int64, device=C.device))
+    c_lo = sum(int(t.item()) for t in lens[:g])
+    return C, Cv, c_lo

@@ -43,6 +43,11 @@ class OracleOps:
         pts.sort(key=lambda ab: (ab[0] + ab[1], ab[0]))
         return pts + [(n, m)]
 
+    def sort(self, K, Kv):
+        v = np.zeros(K.numel(), np.uint32) if Kv is None else Kv.numpy().view(np.uint32)
+        k, sv = oracle.merge_sort(K.numpy(), v, run=32)
+        return torch.from_numpy(k.copy()), (None if Kv is None else torch.from_numpy(sv.view(np.int32).copy()))
+
     def merge(self, A, Av, B, Bv):
         a, b = A.numpy(), B.numpy()
         if Av is None:
@@ -106,7 +111,7 @@ def run_threads(G, A, Av, B, Bv, ca, cb, keys_only=False):
                                              hub.comm(g), OracleOps())
         except Exception as e:                       # noqa: BLE001
             errors.append(e)
-            hub.barrier.abort()
+            hub.abort()
 
     ts = [threading.Thread(target=worker, args=(g,)) for g in range(G)]
     for t in ts:
@@ -159,3 +164,87 @@ def test_gloo_process_groups(world, tmp_path):
     results = [torch.load(os.path.join(tmp_path, f"r{g}.pt"), weights_only=False) for g in range(world)]
     A, Av, B, Bv = make_case(77 + world, 2500, 1800, 40)
     check(world, A, Av, B, Bv, results)
+
+
+def sort_case(seed, total, alphabet, G):
+    g = torch.Generator().manual_seed(seed)
+    K = torch.randint(0, alphabet, (total,), generator=g, dtype=torch.int32)
+    Kv = torch.arange(total, dtype=torch.int32)
+    return K, Kv, cuts(total, G, seed + 1)
+
+
+def check_sort(G, K, Kv, results, keys_only=False):
+    OK, OV = oracle.merge_sort(K.numpy(), Kv.numpy().view(np.uint32), run=1)
+    pos = 0
+    for g in range(G):
+        C, Cv, c_lo = results[g]
+        assert c_lo == pos
+        assert np.array_equal(C.numpy(), OK[pos:pos + C.numel()])
+        if not keys_only:
+            assert np.array_equal(Cv.numpy().view(np.uint32), OV[pos:pos + C.numel()])
+        pos += C.numel()
+    assert pos == K.numel()
+
+
+def run_sort_threads(G, K, Kv, cuts_, keys_only=False):
+    hub = D.ThreadHub(G)
+    results, errors = [None] * G, []
+
+    def worker(g):
+        try:
+            results[g] = D.sort_distributed(K[cuts_[g]:cuts_[g + 1]],
+                                            None if keys_only else Kv[cuts_[g]:cuts_[g + 1]],
+                                            hub.comm(g), OracleOps())
+        except Exception as e:                       # noqa: BLE001
+            errors.append(e)
+            hub.abort()
+
+    ts = [threading.Thread(target=worker, args=(g,)) for g in range(G)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    return results
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("total,alphabet", [(0, 3), (1, 3), (5000, 7), (12001, 100000), (3000, 1)])
+def test_sort_thread_ranks_against_the_oracle(G, total, alphabet):
+    """Every rank's slice sorted locally, then rounds of distributed merges
+    of neighbouring groups (G not a power of two leaves a group without a
+    right half in some rounds); the pieces in rank order are the oracle's
+    stable sort of the whole array, equal keys in their global order."""
+    K, Kv, c = sort_case(total * 3 + G + alphabet, total, alphabet, G)
+    check_sort(G, K, Kv, run_sort_threads(G, K, Kv, c))
+
+
+def test_sort_thread_ranks_keys_only():
+    K, Kv, c = sort_case(4, 7000, 50, 4)
+    check_sort(4, K, Kv, run_sort_threads(4, K, Kv, c, keys_only=True), keys_only=True)
+
+
+def _gloo_sort_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        K, Kv, c = sort_case(91 + world, 6000, 300, world)
+        res = D.sort_distributed(K[c[rank]:c[rank + 1]], Kv[c[rank]:c[rank + 1]], D.TorchComm(), OracleOps())
+        torch.save(res, os.path.join(out_dir, f"s{rank}.pt"))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_sort_gloo_process_groups(world, tmp_path):
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_gloo_sort_worker, args=(world, port, str(tmp_path)), nprocs=world, start_method="spawn")
+    results = [torch.load(os.path.join(tmp_path, f"s{g}.pt"), weights_only=False) for g in range(world)]
+    K, Kv, _ = sort_case(91 + world, 6000, 300, world)
+    check_sort(world, K, Kv, results)

@@ -37,7 +37,7 @@ def run(G, kt, A, Av, B, Bv, ca, cb, cfg=None):
                                              D.GpuOps(kt, cfg))
         except Exception as e:                       # noqa: BLE001
             errors.append(e)
-            hub.barrier.abort()
+            hub.abort()
 
     ts = [threading.Thread(target=worker, args=(g,)) for g in range(G)]
     for t in ts:
@@ -84,3 +84,60 @@ def test_distributed_merge_keys_only_and_wide_payloads():
     res = run(G, "u32", A.to(DEV), Aw, B.to(DEV), Bw, ca, cb)
     got = np.concatenate([r[1].cpu().numpy().view(np.uint64) for r in res])
     assert np.array_equal(got >> np.uint64(32), V.astype(np.uint64))
+
+
+def run_sort(G, kt, K, Kv, c, cfg=None):
+    hub = D.ThreadHub(G)
+    results, errors = [None] * G, []
+
+    def worker(g):
+        try:
+            torch.cuda.set_device(0)
+            results[g] = D.sort_distributed(K[c[g]:c[g + 1]], None if Kv is None else Kv[c[g]:c[g + 1]],
+                                            hub.comm(g), D.GpuOps(kt, cfg))
+        except Exception as e:                       # noqa: BLE001
+            errors.append(e)
+            hub.abort()
+
+    ts = [threading.Thread(target=worker, args=(g,)) for g in range(G)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    return results
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 4])
+@pytest.mark.parametrize("kt,total", [("u64", 300007), ("i32", 99991), ("f32", 4096 * 5 + 1), ("u32", 0)])
+def test_distributed_sort_threads_against_the_oracle(G, kt, total):
+    """Local tm_merge_sort of every rank's slice, then distributed merges of
+    neighbouring groups of ranks; the pieces in rank order are the oracle's
+    stable sort of the whole array."""
+    g = torch.Generator().manual_seed(total + G)
+    raw = torch.randint(-3000, 3000, (total,), generator=g, dtype=torch.int64)
+    K = {"u64": raw + 3000, "i32": raw.to(torch.int32), "f32": (raw * 0.5).to(torch.float32),
+         "u32": raw.to(torch.int32)}[kt]
+    Kv = W.payload(0, total, "cpu")
+    rng = np.random.default_rng(G + total)
+    c = [0] + sorted(int(v) for v in rng.integers(0, total + 1, G - 1)) + [total]
+    res = run_sort(G, kt, K.to(DEV), Kv.to(DEV), c)
+    OK, OV = oracle.merge_sort(to_np(K, kt), vals_np(Kv), run=1)
+    pos = 0
+    for r in range(G):
+        C, Cv, c_lo = res[r]
+        assert c_lo == pos
+        assert np.array_equal(to_np(C, kt), OK[pos:pos + C.numel()])
+        assert np.array_equal(vals_np(Cv), OV[pos:pos + C.numel()])
+        pos += C.numel()
+    assert pos == total
+
+
+def test_distributed_sort_keys_only():
+    total, G = 50000, 3
+    g = torch.Generator().manual_seed(1)
+    K = torch.randint(0, 77, (total,), generator=g, dtype=torch.int64)
+    res = run_sort(G, "u64", K.to(DEV), None, [0, 20000, 20000, total])
+    got = np.concatenate([to_np(r[0], "u64") for r in res])
+    assert np.array_equal(got, np.sort(to_np(K, "u64"), kind="stable"))
