@@ -407,7 +407,7 @@ def compact_line(line: dict, peak_gbs: float) -> dict:
     cpu = line.get("cpu_baseline")
     if isinstance(cpu, dict):
         c = {k: _r(cpu.get(k)) for k in ("value", "unit", "cores", "kind")}
-        c["sample"] = "the eight merges once, two-pointer oracle"
+        c["sample"] = "8 merges once, two-pointer oracle"
         c["e2e_outputs_equal_oracle"] = cpu.get("e2e_outputs_equal_oracle")
         pp = cpu.get("paper_parallel")
         if isinstance(pp, dict):
@@ -979,6 +979,8 @@ def main():
     ap.add_argument("--no-skewed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, merge-sort and learned forms")
+    ap.add_argument("--serial", action="store_true",
+                    help="run each merge's search, plan and merge back to back on one stream (no overlap)")
     ap.add_argument("--form", default="", choices=["", "batched", "sort", "learned", "small", "search", "keys",
                                                    "partition", "payload64", "segmented"],
                     help="run one form alone (profiling)")
@@ -1067,29 +1069,60 @@ def main():
     search_bytes_per_step = sum(it["p"] * 4 * (int(it["n"]).bit_length() + int(it["m"]).bit_length())
                                 for it in items)
 
-    # per-merge events: search start, plan start, merge start, merge end
-    def step(evs=None):
+    # Steps 1-2 and the selection of every merge run on a second stream, ahead
+    # of the merges on `stream`: merge k waits for its own records only, so
+    # the searches and plans of the later merges overlap the earlier merges
+    # (the eight merges are independent).  A merge's records are rewritten
+    # by the next step only after that merge has read them.  --serial runs
+    # every merge's three phases back to back on one stream instead.
+    s_side = side_stream(dev)
+    merged_ev = [None] * len(items)
+
+    # per-merge events: search start, plan start, plan end (on s_plan), merge
+    # start, merge end (on stream)
+    def step(evs=None, serial=args.serial):
+        s_plan = stream if serial else s_side
+        ready = []
         for k, it in enumerate(items):
             n, m, p = it["n"], it["m"], it["p"]
+            if merged_ev[k] is not None and s_plan is not stream:
+                s_plan.wait_event(merged_ev[k])
             if evs is not None:
-                evs[k][0].record(stream)
-            tm.tm_cross_ranks("i32", it["A"], it["B"], p, it["xbar"], it["ybar"], stream=stream)
+                evs[k][0].record(s_plan)
+            tm.tm_cross_ranks("i32", it["A"], it["B"], p, it["xbar"], it["ybar"], stream=s_plan)
             if evs is not None:
-                evs[k][1].record(stream)
-            tm.tm_plan_subproblems(n, m, p, it["xbar"], it["ybar"], it["tiles"], cfg=cfg, stream=stream)
+                evs[k][1].record(s_plan)
+            tm.tm_plan_subproblems(n, m, p, it["xbar"], it["ybar"], it["tiles"], cfg=cfg, stream=s_plan)
             if evs is not None:
-                evs[k][2].record(stream)
-            tm.tm_merge_tiles("i32", it["A"], it["Av"], it["B"], it["Bv"], it["tiles"], it["count"], it["cap"],
-                              C[:n + m], Cv[:n + m], control, cfg=cfg, stream=stream)
-            if evs is not None:
-                evs[k][3].record(stream)
+                evs[k][2].record(s_plan)
+            if s_plan is stream:
+                merge_one(k, it, evs)
+            else:
+                r = torch.cuda.Event()
+                r.record(s_plan)
+                ready.append(r)
+        for k, it in enumerate(items if s_plan is not stream else []):
+            stream.wait_event(ready[k])
+            merge_one(k, it, evs)
+
+    def merge_one(k, it, evs):
+        n, m = it["n"], it["m"]
+        if evs is not None:
+            evs[k][3].record(stream)
+        tm.tm_merge_tiles("i32", it["A"], it["Av"], it["B"], it["Bv"], it["tiles"], it["count"], it["cap"],
+                          C[:n + m], Cv[:n + m], control, cfg=cfg, stream=stream)
+        if evs is not None:
+            evs[k][4].record(stream)
+        d = torch.cuda.Event()
+        d.record(stream)
+        merged_ev[k] = d
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
     assert tm.tm_read_status(control) == 0
 
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in items] for _ in range(args.steps)]
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in items] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
@@ -1098,6 +1131,7 @@ def main():
     torch.cuda.synchronize(dev)
     with sampler:
         t_start.record(stream)
+        s_side.wait_event(t_start)
         for s in range(args.steps):
             step(evs[s])
         t_end.record(stream)
@@ -1106,10 +1140,17 @@ def main():
         dist.barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
     assert tm.tm_read_status(control) == 0
+    # the merge kernel alone: a few steps with the phases back to back
+    evs_alone = [[[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in items] for _ in range(3)]
+    for s in range(3):
+        step(evs_alone[s], serial=True)
+    torch.cuda.synchronize(dev)
+    assert tm.tm_read_status(control) == 0
+    merge_alone_ms = sum(e[3].elapsed_time(e[4]) for st in evs_alone for e in st) / 3
     search_ms = sum(e[0].elapsed_time(e[1]) for st in evs for e in st)
     plan_ms = sum(e[1].elapsed_time(e[2]) for st in evs for e in st)
-    merge_ms = sum(e[2].elapsed_time(e[3]) for st in evs for e in st)
-    per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][2].elapsed_time(evs[s][k][3]) for s in range(args.steps)]))
+    merge_ms = sum(e[3].elapsed_time(e[4]) for st in evs for e in st)
+    per_item_merge_ms = {it["name"]: float(np.mean([evs[s][k][3].elapsed_time(evs[s][k][4]) for s in range(args.steps)]))
                          for k, it in enumerate(items)}
 
     elapsed_max = max_over_ranks(elapsed_ms, dev)
@@ -1124,13 +1165,17 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "traffic": traffic, "traffic_source": traffic_src,
                 "algorithmic_bytes_per_launch": bytes_merge_per_step / len(items),
+                # kernel time of the searches and plans against all three
+                # (with the overlap they run beside the merges)
                 "search_share": search_ms / (search_ms + plan_ms + merge_ms),
                 "plan_share": plan_ms / (search_ms + plan_ms + merge_ms),
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                # the same kernel with no search or plan running beside it
+                "frac_alone": bytes_merge_per_step / (merge_alone_ms / 1e3) / 1e9 / peak,
                 # whole step: merge bytes plus the searches' probe bytes (one
-                # 4-byte key per probe) over search + plan + merge time
+                # 4-byte key per probe) over the step's wall time
                 "step_frac": (bytes_merge_per_step + search_bytes_per_step) * args.steps /
-                             ((search_ms + plan_ms + merge_ms) / 1e3) / 1e9 / peak}
+                             (elapsed_ms / 1e3) / 1e9 / peak}
 
     # End to end: pinned host inputs -> device, merge through tm_merge, result
     # -> host, for every merge of the step.  Copies in, merges and copies out
@@ -1236,8 +1281,9 @@ def main():
                            "merges_per_step": n_merges, "tile": args.tile or 2048,
                            "blocks_p": p_first,
                            "threads": args.threads or 128, "stages": args.stages or "auto",
-                           "split": {0: "diagonal (default)", 1: "blocks", 2: "diagonal"}[args.split],
-                           "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+                           "split": {0: "diagonal", 1: "blocks", 2: "diagonal"}[args.split],
+                           "l2": "inputs > L2", "parallelism": f"replicas x{world}",
+                           "phases": "serial" if args.serial else "overlap"},
                 "forms": forms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * n_merges * args.steps}

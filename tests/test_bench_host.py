@@ -138,13 +138,13 @@ def test_compact_line_keeps_every_form_and_stays_short():
             "data": "synthetic",
             "config": {"workload": bench.WORKLOAD_SHORT, "elements_per_step": 3222274048, "merges_per_step": 8,
                        "tile": 2048, "blocks_p": 262144, "threads": 128, "stages": "auto",
-                       "split": "diagonal (default)", "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+                       "split": "diagonal", "l2": "inputs > L2", "parallelism": "replicas x1", "phases": "overlap"},
             "forms": _full_forms(),
             "roofline": {"bound": "hbm", "kernel": "merge_engine_kernel", "achieved": 6760.0065, "peak": 6703.8,
                          "unit": "GB/s", "frac": 1.0083, "peak_kind": "measured hbm_gbs (copy)",
                          "traffic": 6162599116.8, "traffic_source": "profiles/merge_engine_kernel_large_merge.md",
                          "algorithmic_bytes_per_launch": 6444548096.0, "search_share": 0.0385,
-                         "plan_share": 0.0145, "frac_of_nominal": 0.845, "step_frac": 0.95},
+                         "plan_share": 0.0145, "frac_of_nominal": 0.845, "frac_alone": 1.0102, "step_frac": 0.95},
             "cpu_baseline": {"value": 7.0e8, "unit": "elems/s", "cores": 1, "kind": "oracle", "sample": "y" * 200,
                              "seconds": 4.6, "e2e_outputs_equal_oracle": True,
                              "paper_parallel": {"value": 9.6e9, "cores": 16, "sample": "z" * 100}},
