@@ -181,6 +181,21 @@ def make_inputs(device, log2n=28, dists=None, skewed_too=True):
     return items
 
 
+def headline_config(args, world: int, lengths: list, p=None) -> dict:
+    """The large-merge workload's config, the same on both arms; lengths:
+    (n, m) of every merge of a step; p: the first merge's block count (the
+    library's default, one block per tile of outputs, when not given)."""
+    n0, m0 = lengths[0]
+    tile = args.tile or 2048
+    return {"workload": WORKLOAD_SHORT, "elements_per_step": sum(n + m for n, m in lengths),
+            "merges_per_step": len(lengths), "tile": tile,
+            "blocks_p": p if p is not None else -(-(n0 + m0) // tile),
+            "threads": args.threads or 128, "stages": args.stages or "auto",
+            "split": {0: "diagonal", 1: "blocks", 2: "diagonal"}[args.split],
+            "l2": "inputs > L2", "parallelism": f"replicas x{world}",
+            "phases": "serial" if args.serial else "overlap"}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle on the host cores (rank 0 only; other ranks exit).
 
@@ -227,7 +242,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": headline_config(args, world, [(len(h[0]), len(h[2])) for h in hosts]),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -1257,7 +1272,7 @@ def main():
 
     clocks = sampler.summary(power_floor_w=200.0)
     forms = None
-    n_merges, p_first = len(items), items[0]["p"]
+    n_merges, lengths, p_first = len(items), [(it["n"], it["m"]) for it in items], items[0]["p"]
     if not args.no_forms:
         for it in items:
             it.clear()
@@ -1277,13 +1292,7 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": elapsed_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD_SHORT, "elements_per_step": elems_per_step,
-                           "merges_per_step": n_merges, "tile": args.tile or 2048,
-                           "blocks_p": p_first,
-                           "threads": args.threads or 128, "stages": args.stages or "auto",
-                           "split": {0: "diagonal", 1: "blocks", 2: "diagonal"}[args.split],
-                           "l2": "inputs > L2", "parallelism": f"replicas x{world}",
-                           "phases": "serial" if args.serial else "overlap"},
+                "config": headline_config(args, world, lengths, p_first),
                 "forms": forms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 3 * n_merges * args.steps}
