@@ -689,11 +689,12 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
             "bit_exact": same}
 
 
-def bench_sort(dev, steps: int = 3, cfg=None):
+def bench_sort(dev, steps: int = 3, cfg=None, log2n: int = 28):
     """Stable merge sort of 2**28 u64 keys uniform in [0, 2**24) with u32
-    payloads (original index): sorted runs of 4096, then 16 merge rounds."""
+    payloads (original index): sorted runs of 4096, then 16 merge rounds.
+    (log2n < 28: a smaller case of the same kernels, for profiles.)"""
     from paper_1202_6575_gb300 import tm, workloads as W
-    src_k, src_v = W.sort_input(dev)
+    src_k, src_v = W.sort_input(dev, n=1 << log2n)
     n = src_k.numel()
     keys, vals = torch.empty_like(src_k), torch.empty_like(src_v)
     tk, tv = torch.empty_like(src_k), torch.empty_like(src_v)
@@ -745,7 +746,7 @@ def bench_sort(dev, steps: int = 3, cfg=None):
         r *= 2
         rounds += 1
     moved = n * 24 * (rounds + 1)                     # run formation + every round read and write 12 B
-    return {"workload": "stable merge sort of 2^28 u64 keys uniform in [0, 2^24) + u32 payloads",
+    return {"workload": f"stable merge sort of 2^{log2n} u64 keys uniform in [0, 2^24) + u32 payloads",
             "elements": n, "value": n / (ms / 1e3), "unit": "sorted elems/s", "ms": ms, "rounds": rounds,
             "config": best, "passes_gbs": moved / (ms / 1e3) / 1e9,
             "frac_of_hbm": moved / (ms / 1e3) / 1e9 / measured_peaks()[0],
@@ -1022,7 +1023,7 @@ def main():
         elif args.form == "sort":
             fixed = {k: v for k, v in (("tile", args.tile), ("threads", args.threads), ("stages", args.stages),
                                        ("split", args.split)) if v} or None
-            out = bench_sort(dev, cfg=fixed)
+            out = bench_sort(dev, cfg=fixed, log2n=args.log2n)
         elif args.form == "small":
             out = bench_small_merge(dev)
         elif args.form == "search":
