@@ -172,7 +172,9 @@ TM_API tm_status tm_read_status(const void* status, tm_stream_t stream);
 /* Single merge (Section 2, Steps 1-4)                                       */
 /* ------------------------------------------------------------------------ */
 
-/* The number of blocks p that tm_merge uses for (n, m, cfg). */
+/* The number of blocks p that tm_merge uses for (n, m, cfg) when payloads
+ * are given (keys-only merges above the fused range may use fewer: see
+ * tm_merge). */
 TM_API int64_t tm_merge_blocks(int64_t n, int64_t m, const tm_config* cfg);
 
 /* Workspace bytes tm_merge needs: a 256-byte control block (status word,
@@ -191,11 +193,14 @@ TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg
  * run instead as one cooperative launch of the tile kernel: its warps do
  * the 2p searches (one warp per search, 32 probes per round), a grid-wide
  * barrier (bounded wait: TM_ERR_TIMEOUT) stands for the synchronisation,
- * the grid writes the 2p tile records (Steps 3-4 selection) into the
- * workspace, a second barrier follows, and the CTAs merge the records from
- * the work queue; the result is identical.  cfg->unfused = 1 keeps the
- * separate launches.  The control block (status word in its first 4 bytes)
- * is cleared by this call. */
+ * and each CTA then selects the subproblems of its own processing elements
+ * (Steps 3-4) and merges them; the result is identical.  cfg->unfused = 1
+ * keeps the separate launches.  Keys-only merges (all payload pointers
+ * NULL) above that range, with no cfg field set but payload_bytes and
+ * merge_ways, use 8192-element tiles and 256 consumer threads, so fewer
+ * blocks than tm_merge_blocks reports (the workspace size covers them).
+ * The control block (status word in its first 4 bytes) is cleared by this
+ * call. */
 TM_API tm_status tm_merge(tm_key_type kt,
                    const void* a_keys, const uint32_t* a_vals, int64_t n,
                    const void* b_keys, const uint32_t* b_vals, int64_t m,

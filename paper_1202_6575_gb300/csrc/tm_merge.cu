@@ -2,6 +2,7 @@
 // and the staged tile-merge kernel (Steps 3-4), plus their C-ABI entry
 // points.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -394,6 +395,32 @@ static bool fused_applies(int64_t p, int64_t cap, const tm_config* cfg) {
     return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop;
 }
 
+// Keys-only merges beyond the fused launch's range, called with the default
+// configuration, take larger tiles and 256 consumer threads: without payload
+// regions the stages of 8192-element tiles still fit two CTAs per SM, and
+// the longer per-thread runs spread the co-rank search and the per-tile
+// work over more outputs (n = m = 2^28 int32 keys: uniform keys 0.90 -> 0.83
+// ms, keys in [0, 1024) 0.69 -> 0.67 ms).  The block count p then follows
+// the larger tile, so the default workspace size still covers it.
+constexpr int kKeysOnlyTile = 8192;
+constexpr int kKeysOnlyThreads = 256;
+
+static bool keys_only_config(const void* a_vals, const void* b_vals, int64_t n, int64_t m, const tm_config* cfg,
+                             tm_config* out) {
+    if (a_vals != nullptr || b_vals != nullptr) return false;
+    if (cfg) {                                         // nothing set but fields that do not apply here
+        tm_config d{};
+        d.payload_bytes = cfg->payload_bytes;
+        d.merge_ways = cfg->merge_ways;
+        if (std::memcmp(&d, cfg, sizeof(tm_config)) != 0) return false;
+    }
+    if (choose_blocks(n, m, cfg) <= kFusedMaxBlocks) return false;
+    *out = cfg ? *cfg : tm_config{};
+    out->tile = kKeysOnlyTile;
+    out->threads = kKeysOnlyThreads;
+    return true;
+}
+
 template <typename K>
 static tm_status merge_typed(tm_key_type kt, const void* a_keys, const uint32_t* a_vals, int64_t n,
                              const void* b_keys, const uint32_t* b_vals, int64_t m,
@@ -535,9 +562,14 @@ tm_status tm_merge(tm_key_type kt,
     if ((n > 0 && !aligned(a_keys, E)) || (m > 0 && !aligned(b_keys, E)) || (n + m > 0 && !aligned(c_keys, E)) ||
         !payloads_ok(n, a_vals, m, b_vals, c_vals, payload_size(cfg)))
         return TM_ERR_INVALID;
-    const int64_t p = choose_blocks(n, m, cfg);
+    int64_t p = choose_blocks(n, m, cfg);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p, cfg))
         return TM_ERR_WORKSPACE;
+    tm_config keys_cfg;
+    if (keys_only_config(a_vals, b_vals, n, m, cfg, &keys_cfg)) {   // fewer blocks: the workspace covers them
+        cfg = &keys_cfg;
+        p = choose_blocks(n, m, cfg);
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (kt) {
         case TM_KEY_U32: return merge_typed<uint32_t>(kt, a_keys, a_vals, n, b_keys, b_vals, m, c_keys, c_vals, workspace, p, cfg, s);

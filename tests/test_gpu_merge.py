@@ -172,6 +172,33 @@ def test_keys_only_merge(kt, n, m, cfg):
 
 
 @pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
+@pytest.mark.parametrize("n,m,alphabet", [(1 << 25, (1 << 25) + 17, 300), ((1 << 25) - 5, 1 << 25, None),
+                                          (40_000_000, 3, None)])
+def test_keys_only_merge_beyond_the_fused_range(kt, n, m, alphabet):
+    """Keys-only merges above the fused launch's range with the default
+    configuration take 8192-element tiles and 256 consumer threads (fewer
+    blocks than the default sizing, which the workspace covers); every key
+    equals the oracle's merge."""
+    A, Av, B, Bv = W.small_merge(n, m, kt, seed=n + m, alphabet=alphabet, device=DEV)
+    ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m), DEV)
+    C, Cv, ws = tm.tm_merge(kt, A, None, B, None, workspace=ws)
+    assert Cv is None and tm.tm_read_status(ws) == 0
+    K, _ = oracle.merge_two_pointer(to_np(A, kt), vals_np(Av), to_np(B, kt), vals_np(Bv))
+    assert first_mismatch(to_np(C, kt), K) is None
+
+
+@pytest.mark.parametrize("n,m", [(8191, 8193), (100003, 77777), (1 << 17, 5)])
+def test_keys_only_merge_wide_tiles(n, m):
+    """The keys-only large-merge configuration (tile 8192, 256 threads) set
+    explicitly, at sizes with ragged tiles."""
+    A, Av, B, Bv = W.small_merge(n, m, "u64", seed=n, alphabet=500)
+    C, Cv, ws = tm.tm_merge("u64", A.to(DEV), None, B.to(DEV), None, cfg={"tile": 8192, "threads": 256})
+    assert Cv is None and tm.tm_read_status(ws) == 0
+    K, _ = oracle.merge_two_pointer(to_np(A, "u64"), vals_np(Av), to_np(B, "u64"), vals_np(Bv))
+    assert first_mismatch(to_np(C, "u64"), K) is None
+
+
+@pytest.mark.parametrize("kt", ["u32", "i32", "u64", "f32"])
 @pytest.mark.parametrize("n,m,tile", [(0, 5, 64), (7, 0, 64), (1, 1, 64), (5000, 3001, 256),
                                       (100003, 77777, 2048), (1 << 16, 3, 1000), (3, 1 << 16, 4096)])
 def test_equal_output_partition_ablation(kt, n, m, tile):
