@@ -195,10 +195,11 @@ TM_API size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg
  * barrier (bounded wait: TM_ERR_TIMEOUT) stands for the synchronisation,
  * and each CTA then selects the subproblems of its own processing elements
  * (Steps 3-4) and merges them; the result is identical.  cfg->unfused = 1
- * keeps the separate launches.  Keys-only merges (all payload pointers
- * NULL) above that range, with no cfg field set but payload_bytes and
- * merge_ways, use 8192-element tiles and 256 consumer threads, so fewer
- * blocks than tm_merge_blocks reports (the workspace size covers them).
+ * keeps the separate launches.  Above that range, with no cfg field set
+ * but payload_bytes and merge_ways, keys-only merges (all payload pointers
+ * NULL) use 8192-element tiles and 256 consumer threads, so fewer blocks
+ * than tm_merge_blocks reports (the workspace size covers them), and merges
+ * of 8-byte payloads use 256 consumer threads.
  * The control block (status word in its first 4 bytes) is cleared by this
  * call. */
 TM_API tm_status tm_merge(tm_key_type kt,

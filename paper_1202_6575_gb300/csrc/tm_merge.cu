@@ -395,19 +395,22 @@ static bool fused_applies(int64_t p, int64_t cap, const tm_config* cfg) {
     return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop;
 }
 
-// Keys-only merges beyond the fused launch's range, called with the default
-// configuration, take larger tiles and 256 consumer threads: without payload
-// regions the stages of 8192-element tiles still fit two CTAs per SM, and
-// the longer per-thread runs spread the co-rank search and the per-tile
-// work over more outputs (n = m = 2^28 int32 keys: uniform keys 0.90 -> 0.83
-// ms, keys in [0, 1024) 0.69 -> 0.67 ms).  The block count p then follows
-// the larger tile, so the default workspace size still covers it.
+// Merges beyond the fused launch's range, called with the default
+// configuration, get the shape measured best for their layout (n = m = 2^28
+// int32 keys): keys only take 8192-element tiles and 256 consumer threads
+// (without payload regions such stages still fit two CTAs per SM, and the
+// longer per-thread runs spread the co-rank search and the per-tile work:
+// uniform keys 0.90 -> 0.83 ms, keys in [0, 1024) 0.69 -> 0.67 ms); 8-byte
+// payloads take 256 consumer threads (uniform keys 2.07 -> 1.99 ms).  The
+// block count p follows the tile, never above the default one, so the
+// default workspace size still covers it.
 constexpr int kKeysOnlyTile = 8192;
-constexpr int kKeysOnlyThreads = 256;
+constexpr int kWideThreads = 256;
 
-static bool keys_only_config(const void* a_vals, const void* b_vals, int64_t n, int64_t m, const tm_config* cfg,
-                             tm_config* out) {
-    if (a_vals != nullptr || b_vals != nullptr) return false;
+static bool layout_config(const void* a_vals, const void* b_vals, int64_t n, int64_t m, const tm_config* cfg,
+                          tm_config* out) {
+    const bool keys_only = a_vals == nullptr && b_vals == nullptr;
+    if (!keys_only && payload_size(cfg) != 8) return false;
     if (cfg) {                                         // nothing set but fields that do not apply here
         tm_config d{};
         d.payload_bytes = cfg->payload_bytes;
@@ -416,8 +419,8 @@ static bool keys_only_config(const void* a_vals, const void* b_vals, int64_t n, 
     }
     if (choose_blocks(n, m, cfg) <= kFusedMaxBlocks) return false;
     *out = cfg ? *cfg : tm_config{};
-    out->tile = kKeysOnlyTile;
-    out->threads = kKeysOnlyThreads;
+    if (keys_only) out->tile = kKeysOnlyTile;
+    out->threads = kWideThreads;
     return true;
 }
 
@@ -565,9 +568,9 @@ tm_status tm_merge(tm_key_type kt,
     int64_t p = choose_blocks(n, m, cfg);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < merge_workspace_bytes(p, cfg))
         return TM_ERR_WORKSPACE;
-    tm_config keys_cfg;
-    if (keys_only_config(a_vals, b_vals, n, m, cfg, &keys_cfg)) {   // fewer blocks: the workspace covers them
-        cfg = &keys_cfg;
+    tm_config shaped;
+    if (layout_config(a_vals, b_vals, n, m, cfg, &shaped)) {   // p no larger: the workspace covers it
+        cfg = &shaped;
         p = choose_blocks(n, m, cfg);
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

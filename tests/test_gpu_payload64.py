@@ -50,6 +50,13 @@ def test_payload64_merges(kt, n, m, cfg):
 
 
 @pytest.mark.parametrize("kt", ["u32", "u64"])
+def test_payload64_merge_beyond_the_fused_range(kt):
+    """Above the fused launch's range the default merge of 8-byte payloads
+    runs 256 consumer threads; every key and payload equals the oracle's."""
+    merge64_check(kt, (1 << 25) + 5, 1 << 24, None, seed=3, alphabet=None)
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
 def test_payload64_batched(kt):
     g = torch.Generator().manual_seed(5)
     pairs = 3000
