@@ -31,8 +31,8 @@
 namespace pmerge {
 
 constexpr int kSortRun = 4096;
-constexpr int kSortThreads = 512;
-constexpr int kSortVT = kSortRun / kSortThreads;          // 8 items per thread
+constexpr int kSortThreads = 256;                         // two CTAs per SM at 128 registers a thread
+constexpr int kSortVT = kSortRun / kSortThreads;          // 16 items per thread
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixBits = 8;
 constexpr int kRadixDigits = 1 << kRadixBits;
