@@ -514,7 +514,8 @@ def bench_small_merge(dev, steps: int = 200):
     ws = tm.new_workspace(tm.tm_merge_workspace_size(n, m, cfg), dev)
     phases = []
     for i in range(23):
-        flush.fill_(i & 255)
+        with torch.cuda.stream(s):                     # the flush ends before the traced merge starts
+            flush.fill_(i & 255)
         tm.tm_merge("u32", A, Av, B, Bv, C, Cv, ws, cfg=cfg, stream=s)
         ph = tm.tm_merge_phase_times(ws, n, m, cfg, stream=s)
         if i >= 3:
@@ -669,6 +670,7 @@ def bench_batched(dev, steps: int = 10, pairs: int = 65536, with_plain: bool = T
         ref = (C.clone(), Cv.clone())                 # the graph's output
         C.fill_(-1)
         Cv.fill_(-1)
+        s.wait_stream(torch.cuda.current_stream(dev))  # the merges on s write after the fills
         plain()
         s.synchronize()
         same = bool(torch.equal(ref[0], C) and torch.equal(ref[1], Cv))
@@ -954,7 +956,8 @@ def bench_search(dev, log2_base: int = 28, log2_batch: int = 20, reps: int = 30)
     def timed(fn):
         ts = []
         for r in range(reps):
-            flush.fill_(r & 255)
+            with torch.cuda.stream(s):                 # on the timed stream: the flush ends before e0,
+                flush.fill_(r & 255)                   # and the search is enqueued while it runs
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             fn()
