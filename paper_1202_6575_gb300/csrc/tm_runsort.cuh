@@ -170,7 +170,7 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
     for (int j = 0; j < kSortWarps; ++j) { any |= red[j]; all &= red2[j]; }
     const U diff = any ^ all;
 
-    bool in_smem = false;                              // the current order is in sk/sv, not in k/v
+    bool in_smem = false;                              // the current key order is in sk, not only in k
     int* hw = hist + w * kRadixDigits;
     for (int sh = 0; sh < (int)(8 * sizeof(U)); sh += kRadixBits) {
         if (((diff >> sh) & (U)(kRadixDigits - 1)) == 0) continue;   // same for the whole CTA
@@ -182,7 +182,7 @@ __device__ __forceinline__ void run_sort_body(const K* __restrict__ in_k, const 
             }
         }
         for (int j = t; j < kRadixDigits * kSortWarps; j += kSortThreads) hist[j] = 0;
-        __syncthreads();                               // counts zeroed; every read of sk/sv done
+        __syncthreads();                               // counts zeroed; every read of sk done
         int dl[kSortVT];                               // digit << 16 | rank among the warp's earlier items of it
 #pragma unroll
         for (int q = 0; q < kSortVT; ++q) {
