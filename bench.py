@@ -523,6 +523,21 @@ def bench_small_merge(dev, steps: int = 200):
     assert tm.tm_read_status(ws, stream=s) == 0
     assert torch.equal(ref[0], C) and torch.equal(ref[1], Cv)
     out["phases_us"] = {k: float(np.median([ph[k] for ph in phases])) for k in tm.PHASES}
+    # the last traced call per CTA: when each CTA passed the barrier, landed
+    # its first tile and finished, against its tile count (the merge phase
+    # ends with the last CTA)
+    tr = tm.tm_merge_trace(ws, n, m, cfg, stream=s).astype(np.int64)
+    t0 = tr[:, 0].min()
+    rel = lambda col: (tr[:, col] - t0) / 1e3
+    done, tiles = rel(5), tr[:, 7]
+    out["per_cta"] = {
+        "ctas": int(tr.shape[0]),
+        "barrier_passed_us": {"median": float(np.median(rel(2))), "max": float(rel(2).max())},
+        "first_tile_us": {"median": float(np.median(rel(6))), "max": float(rel(6).max())},
+        "merges_done_us": {"median": float(np.median(done)), "p90": float(np.percentile(done, 90)),
+                           "max": float(done.max())},
+        "tiles": {int(k): {"ctas": int((tiles == k).sum()), "done_median_us": float(np.median(done[tiles == k]))}
+                  for k in np.unique(tiles)}}
     return out
 
 

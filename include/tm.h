@@ -221,6 +221,19 @@ TM_API tm_status tm_merge(tm_key_type kt,
 TM_API tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
                                       double* us_out, tm_stream_t stream);
 
+/* The per-CTA stamps behind tm_merge_phase_times (same workspace, n, m,
+ * cfg): synchronises `stream` and writes to out (host memory, room for
+ * `capacity` words), for each CTA c of the last traced fused launch, 8
+ * words out[8c .. 8c+7]: %globaltimer nanoseconds at kernel entry, searches
+ * done, grid barrier passed, its own subproblems selected (twice: the
+ * launch has no second barrier), merges done (its last store issued), its
+ * first staged tile landed; then the number of tiles the CTA merged.
+ * *ctas receives the CTA count, also when `capacity` is too small (then
+ * TM_ERR_INVALID and nothing is written; out may be NULL with capacity 0
+ * to ask for the count); otherwise the errors of tm_merge_phase_times. */
+TM_API tm_status tm_merge_trace(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
+                                uint64_t* out, int64_t capacity, int64_t* ctas, tm_stream_t stream);
+
 /* Steps 1 and 2 alone (Section 2): xbar[i] = rank_low(A[x_i], B) for i < p,
  * xbar[p] = m; ybar[j] = rank_high(B[y_j], A) for j < p, ybar[p] = n, with
  * the block starts x_i, y_j of Section 2 (the first n mod p blocks one

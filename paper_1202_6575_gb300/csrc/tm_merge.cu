@@ -525,20 +525,37 @@ size_t tm_merge_workspace_size(int64_t n, int64_t m, const tm_config* cfg) {
     return merge_workspace_bytes(choose_blocks(n, m, cfg), cfg);
 }
 
-tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
-                               double* us_out, tm_stream_t stream) {
-    if (n < 0 || m < 0 || !us_out || !wants_trace(cfg) || !aligned(workspace, 256)) return TM_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+// The stamps of the last traced fused launch on `workspace`: grid CTAs of
+// kTraceSlots words each, after synchronising `stream`.
+tm_status read_trace(const void* workspace, int64_t n, int64_t m, const tm_config* cfg, tm_stream_t stream,
+                     std::vector<uint64_t>& t, uint64_t& grid) {
+    if (n < 0 || m < 0 || !wants_trace(cfg) || !aligned(workspace, 256)) return TM_ERR_INVALID;
     const MergeWs w = merge_ws_layout(const_cast<void*>(workspace), choose_blocks(n, m, cfg), true);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (const cudaError_t e = cudaStreamSynchronize(s); e != cudaSuccess) return cuda_failed(e);
-    uint64_t grid = 0;
+    grid = 0;
     if (const cudaError_t e = cudaMemcpy(&grid, w.trace, 8, cudaMemcpyDeviceToHost); e != cudaSuccess)
         return cuda_failed(e);
     if (grid == 0 || grid > (uint64_t)kTraceMaxCtas) return TM_ERR_INVALID;
-    std::vector<uint64_t> t((size_t)grid * kTraceSlots);
+    t.assign((size_t)grid * kTraceSlots, 0);
     if (const cudaError_t e = cudaMemcpy(t.data(), w.trace + kTraceSlots, t.size() * 8, cudaMemcpyDeviceToHost);
         e != cudaSuccess)
         return cuda_failed(e);
+    return TM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, const tm_config* cfg,
+                               double* us_out, tm_stream_t stream) {
+    if (!us_out) return TM_ERR_INVALID;
+    std::vector<uint64_t> t;
+    uint64_t grid = 0;
+    if (const tm_status st = read_trace(workspace, n, m, cfg, stream, t, grid); st != TM_OK) return st;
     // phase ends: the last CTA to reach each stamp; start: the first entry
     uint64_t start = UINT64_MAX, end[6] = {0, 0, 0, 0, 0, 0};
     for (uint64_t c = 0; c < grid; ++c) {
@@ -550,6 +567,18 @@ tm_status tm_merge_phase_times(const void* workspace, int64_t n, int64_t m, cons
     for (int k = 1; k <= 5; ++k) end[k] = std::max(end[k], end[k - 1]);   // a phase never ends before the last
     for (int k = 0; k < 5; ++k) us_out[k] = (double)(end[k + 1] - end[k]) * 1e-3;
     us_out[5] = (double)(end[5] - start) * 1e-3;
+    return TM_OK;
+}
+
+tm_status tm_merge_trace(const void* workspace, int64_t n, int64_t m, const tm_config* cfg, uint64_t* out,
+                         int64_t capacity, int64_t* ctas, tm_stream_t stream) {
+    if (!ctas || capacity < 0 || (capacity > 0 && !out)) return TM_ERR_INVALID;   // capacity 0: the count only
+    std::vector<uint64_t> t;
+    uint64_t grid = 0;
+    if (const tm_status st = read_trace(workspace, n, m, cfg, stream, t, grid); st != TM_OK) return st;
+    *ctas = (int64_t)grid;
+    if ((uint64_t)capacity < t.size()) return TM_ERR_INVALID;
+    std::copy(t.begin(), t.end(), out);
     return TM_OK;
 }
 

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "tm_subproblems": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _P]),
     "tm_merge_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "tm_merge_phase_times": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _P]),
+    "tm_merge_trace": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _I64, _P, _P]),
     "tm_merge_sort_segmented_workspace_size": (_SZ, [_I64, _P, _I64, _P]),
     "tm_merge_sort_segmented": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P, _P]),
     "tm_merge_batched_workspace_size": (_SZ, [_I64, _I64, _I64, _P]),
@@ -387,6 +388,23 @@ def tm_merge_phase_times(workspace, n: int, m: int, cfg, stream=None) -> dict:
                                        ctypes.cast(out, ctypes.c_void_p), _stream(stream))
     _check(code, "tm_merge_phase_times")
     return dict(zip(PHASES, list(out)))
+
+
+TRACE_SLOTS = ("entry", "searched", "barrier", "selected", "selected2", "merged", "first_tile", "tiles")
+
+
+def tm_merge_trace(workspace, n: int, m: int, cfg, stream=None) -> np.ndarray:
+    """Per-CTA stamps of the last traced fused launch of tm_merge on
+    `workspace` (cfg with trace = 1, same n, m, cfg): uint64 array (CTAs, 8),
+    columns TRACE_SLOTS (%globaltimer nanoseconds, then the tile count)."""
+    ctas = ctypes.c_int64(0)
+    wp = _dev(workspace, "workspace", (torch.uint8,))
+    load().tm_merge_trace(wp, n, m, _cfg(cfg), None, 0, ctypes.byref(ctas), _stream(stream))   # the CTA count
+    out = np.zeros((max(ctas.value, 0), len(TRACE_SLOTS)), dtype=np.uint64)
+    code = load().tm_merge_trace(wp, n, m, _cfg(cfg), out.ctypes.data_as(ctypes.c_void_p), out.size,
+                                 ctypes.byref(ctas), _stream(stream))
+    _check(code, "tm_merge_trace")
+    return out
 
 
 def tm_merge_noalloc(kt: str, A, Av, B, Bv, C, Cv, status=None, cfg=None, stream=None):

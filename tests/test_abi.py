@@ -163,6 +163,15 @@ def test_invalid_arguments_of_the_batched_sort_graph_and_learned_calls(lib):
     ct = tm.TmConfig(trace=1)
     assert lib.tm_merge_phase_times(P(256), 10, 10, ctypes.byref(ct), None, None) == INV
     assert lib.tm_merge_phase_times(P(8), 10, 10, ctypes.byref(ct), ctypes.cast(out6, ctypes.c_void_p), None) == INV
+    # the per-CTA trace: a traced configuration, a count pointer, room or a count-only query
+    cnt = ctypes.c_int64(-1)
+    buf = (ctypes.c_uint64 * 16)()
+    assert lib.tm_merge_trace(P(256), 10, 10, None, buf, 16, ctypes.byref(cnt), None) == INV
+    assert lib.tm_merge_trace(P(256), 10, 10, ctypes.byref(ct), buf, 16, None, None) == INV
+    assert lib.tm_merge_trace(P(256), 10, 10, ctypes.byref(ct), buf, -1, ctypes.byref(cnt), None) == INV
+    assert lib.tm_merge_trace(P(256), 10, 10, ctypes.byref(ct), None, 16, ctypes.byref(cnt), None) == INV
+    assert lib.tm_merge_trace(P(8), 10, 10, ctypes.byref(ct), buf, 16, ctypes.byref(cnt), None) == INV
+    assert cnt.value == -1                                  # refused before anything was read
     # payload words: 4 or 8 bytes; 8-byte words need 8-byte alignment; the
     # learned and allocation-free calls take 4-byte words only
     c8 = tm.TmConfig(payload_bytes=8)

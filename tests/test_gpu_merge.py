@@ -320,6 +320,18 @@ def test_traced_fused_launch_gives_phase_times_and_the_same_merge():
     assert all(v >= 0 for v in ph.values())
     assert ph["merge"] > 0 and ph["search"] > 0
     assert abs(sum(ph[k] for k in tm.PHASES[:5]) - ph["total"]) < 1e-6 * max(1.0, ph["total"]) + 1e-3
+    # the per-CTA stamps behind the phases: ordered within each CTA, the
+    # phase ends are the last CTAs' stamps, and the packed tiles hold every
+    # record (one or more each; this workload's records average 768
+    # elements, so a tile of at most 2176 packs few of them)
+    tr = tm.tm_merge_trace(ws, n, m, cfg).astype(np.int64)
+    assert tr.shape[1] == len(tm.TRACE_SLOTS) and tr.shape[0] >= 1
+    assert np.all(tr[:, 1] >= tr[:, 0]) and np.all(tr[:, 2] >= tr[:, 1]) and np.all(tr[:, 5] >= tr[:, 2])
+    t0 = tr[:, 0].min()
+    assert abs((tr[:, 5].max() - t0) / 1e3 - ph["total"]) < 1e-3
+    assert abs((tr[:, 1].max() - t0) / 1e3 - ph["search"]) < 1e-3
+    R = tm.tm_plan_tile_count(n, m, 1024)
+    assert R // 4 <= tr[:, 7].sum() <= R and tr[:, 7].min() >= 0
     # a separate-launch call records no trace
     cfg_u = {"p": 1024, "trace": 1, "unfused": 1}
     tm.tm_merge("u32", *d, None, None, ws, cfg=cfg_u)
