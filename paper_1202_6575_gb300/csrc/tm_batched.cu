@@ -324,12 +324,24 @@ batched_plan_kernel(PairSet ps, PairBases pb, int64_t total_threads, const int64
     const int64_t pe = a_side ? local : local - p;
     if (a_side ? block_start<int64_t>(n, p, pe) >= n : block_start<int64_t>(m, p, pe) >= m) return;
     const int64_t rb = rank_base_of(ps, pb, k);
-    auto xb = [&](int64_t i) { return __ldg(xbar + rb + i); };
-    auto yb = [&](int64_t j) { return __ldg(ybar + rb + j); };
-    int64_t a0, a1, b0, b1;
-    subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
-    const int64_t chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
-                                 : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
+    int64_t a0, a1, b0, b1, chain;
+    constexpr int64_t kSmall = int64_t(1) << 30;       // block arithmetic of such pairs fits int32
+    if (n < kSmall && m < kSmall && p < kSmall) {       // 32-bit divisions: every pair of a sort round
+        auto xb = [&](int32_t i) { return (int32_t)__ldg(xbar + rb + i); };
+        auto yb = [&](int32_t j) { return (int32_t)__ldg(ybar + rb + j); };
+        int32_t s0, s1, t0, t1;
+        const int32_t pe32 = (int32_t)pe, n32 = (int32_t)n, m32 = (int32_t)m, p32 = (int32_t)p;
+        subproblem_of<int32_t>(a_side, pe32, n32, m32, p32, xb, yb, s0, s1, t0, t1);
+        a0 = s0; a1 = s1; b0 = t0; b1 = t1;
+        chain = a_side ? pe + first_block_at_or_after<int32_t>(m32, p32, xb(pe32))
+                       : pe + first_block_at_or_after<int32_t>(n32, p32, yb(pe32));
+    } else {
+        auto xb = [&](int64_t i) { return __ldg(xbar + rb + i); };
+        auto yb = [&](int64_t j) { return __ldg(ybar + rb + j); };
+        subproblem_of<int64_t>(a_side, pe, n, m, p, xb, yb, a0, a1, b0, b1);
+        chain = a_side ? pe + first_block_at_or_after<int64_t>(m, p, xb(pe))
+                       : pe + first_block_at_or_after<int64_t>(n, p, yb(pe));
+    }
     TileDesc d{};
     d.a0 = a0g + a0; d.b0 = b0g + b0; d.c0 = c0g + a0 + b0;
     d.nA = (int32_t)(a1 - a0); d.nB = (int32_t)(b1 - b0);

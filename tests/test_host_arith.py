@@ -163,3 +163,60 @@ def test_blocks32_equals_the_general_block_arithmetic(lib):
         for k in ks:
             assert lib.h_blocks32_of(length, p, k) == lib.h_block_of64(length, p, k), (length, p, k)
             assert lib.h_blocks32_first(length, p, k) == lib.h_first_block64(length, p, k), (length, p, k)
+
+
+def _selection(lib, width, n, m, p, xbar, ybar):
+    f = lib.h_all_subproblems32 if width == 32 else lib.h_all_subproblems64
+    t = ctypes.c_int32 if width == 32 else ctypes.c_int64
+    P = ctypes.c_void_p
+    f.restype = None
+    f.argtypes = [t, t, t, P, P, P]
+    out = np.zeros((2 * p, 5), dtype=np.int64)
+    xb, yb = np.ascontiguousarray(xbar, dtype=np.int64), np.ascontiguousarray(ybar, dtype=np.int64)
+    f(n, m, p, xb.ctypes.data, yb.ctypes.data, out.ctypes.data)
+    return out
+
+
+def _closed_form_ranks(n, m, p, c1, d1, c2, d2):
+    """Cross ranks of A[i] = floor(i c1 / d1) (n keys) and B[j] = floor(j c2 /
+    d2) (m keys), exactly, without the arrays: #{j : B[j] < v} = min(m,
+    ceil(v d2 / c2)) and #{i : A[i] <= v} = min(n, ceil((v + 1) d1 / c1))."""
+    xs = [oracle.block_start(n, p, k) for k in range(p)]
+    ys = [oracle.block_start(m, p, k) for k in range(p)]
+    xbar = [min(m, -(-((x * c1 // d1) * d2) // c2)) for x in xs] + [m]
+    ybar = [min(n, -(-(((y * c2 // d2) + 1) * d1) // c1)) for y in ys] + [n]
+    return np.array(xbar, dtype=np.int64), np.array(ybar, dtype=np.int64)
+
+
+@pytest.mark.parametrize("n,m,p,c1,d1,c2,d2", [
+    ((1 << 30) - 1, (1 << 30) - 3, 1 << 17, 3, 1, 3, 1),
+    ((1 << 30) - 1, 5, 1 << 16, 1, 1, 7, 2),
+    (999_999_937, 123_456_791, 40_001, 5, 3, 2, 7),
+    (1 << 27, 1 << 27, 131072, 1, 16, 1, 16),
+    (4097, (1 << 29) + 11, 3, 11, 2, 1, 5)])
+def test_selection_in_32_bits_equals_64_bits(lib, n, m, p, c1, d1, c2, d2):
+    """The batched plan kernel selects the subproblems of pairs below 2^30
+    (every pair of a sort round) with 32-bit block arithmetic: the same
+    records and chain indices as the 64-bit path, on exact cross ranks of
+    tie-heavy and tie-free key sequences up to just below 2^30."""
+    xbar, ybar = _closed_form_ranks(n, m, p, c1, d1, c2, d2)
+    a = _selection(lib, 32, n, m, p, xbar, ybar)
+    b = _selection(lib, 64, n, m, p, xbar, ybar)
+    assert np.array_equal(a, b)
+
+
+def test_selection_matches_the_oracles_five_cases_small(lib):
+    """On small sizes both widths give the oracle's subproblems (its
+    literal five cases) from the oracle's cross ranks."""
+    rng = np.random.default_rng(3)
+    for _ in range(60):
+        n, m = int(rng.integers(0, 300)), int(rng.integers(0, 300))
+        p = int(rng.integers(1, 40))
+        A = np.sort(rng.integers(0, 20, n)).astype(np.int32)
+        B = np.sort(rng.integers(0, 20, m)).astype(np.int32)
+        xbar, ybar = oracle.cross_ranks(A, B, p)
+        t = oracle.subproblems(n, m, p, xbar, ybar)      # rows: own range, other side's range
+        want = np.concatenate([t[:p, [0, 1, 2, 3]], t[p:, [2, 3, 0, 1]]])   # as (a0, a1, b0, b1)
+        for width in (32, 64):
+            got = _selection(lib, width, n, m, p, xbar, ybar)
+            assert np.array_equal(got[:, :4], want), (n, m, p, width)
