@@ -91,6 +91,12 @@ def test_reference_arm_json_line_on_a_small_sample():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same config as the library's arm on this workload (its block count
+    # is the library's default, one block per 2048 outputs)
+    n = 1 << 16
+    lengths = [(n, n)] * 4 + [(n, n >> 10)] * 4
+    assert d["config"]["elements_per_step"] == sum(a + b for a, b in lengths)
+    assert d["config"]["blocks_p"] == (2 * n) // 2048 and d["config"]["merges_per_step"] == 8
 
 
 def test_cpu_baselines_of_the_sort_and_batched_forms():
